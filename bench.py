@@ -1,0 +1,336 @@
+"""Benchmark: path.tenor.steps/s of the Levy LIBOR Monte Carlo on GB300.
+
+One step = one pass of the hot path over one batch: the Picard and the full
+Euler schemes (plus the MLP drift when trained weights are available) each
+simulate all paths of the workload and accumulate caplet payoffs.  A unit is
+one (path, live rate, Euler step); rate i is live for i*s steps, so a path of
+the N=40 workload has s*n(n+1)/2 = 6240 units.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 (torchrun): rank r simulates its own 2^20 paths (global path indices
+r*2^20 ...), weak scaling, no collective on the data path; timing is the max
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1006_3340_gb300 import workloads  # noqa: E402
+
+METRIC = "path·tenor·steps/s: Picard vs full Euler vs MLP drift, 1 GB300, ≤0.5bp caplet err"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _workload(args):
+    wl = workloads.large_single(paths=args.paths or (1 << 20))
+    return wl
+
+
+def _describe(wl, schemes):
+    return (f"{wl.name}: N={wl.N} (n={wl.n} rates) delta={wl.delta} s={wl.s} Q={wl.Q} "
+            f"NIG({wl.alpha},{wl.beta},{wl.dbar}) {wl.paths} paths/GPU, "
+            f"{wl.strikes.shape[1]} strikes/maturity, schemes={'+'.join(schemes)}")
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for name, val in zip(names[1:], r[5:9]):
+                if val.lower() in ("active", "0x1") or val == "1":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def cpu_baseline(wl, schemes, budget_s=12.0, threads=None):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    batches of paths (the same global paths the GPU simulates first)
+    alternating schemes until the time budget is used."""
+    from oracle import oracle as ora
+    from oracle import quadrature
+
+    x, W = quadrature.rule_for(wl)
+    model = ora.OracleModel(wl, x, W)
+    threads = threads or os.cpu_count() or 1
+    codes = {"picard": ora.PICARD, "full": ora.FULL, "frozen": ora.FROZEN}
+    batch = 1024
+    units = 0
+    done = {s: 0 for s in schemes}
+    t0 = time.perf_counter()
+    while True:
+        for s in schemes:
+            if s not in codes:
+                continue
+            ora.simulate(model, codes[s], path0=done[s], npaths=batch, threads=threads)
+            done[s] += batch
+            units += batch * wl.units_per_path()
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    sample = ", ".join(f"{s}: paths 0..{done[s] - 1}" for s in done if s in codes)
+    return {"value": units / dt, "unit": "path·tenor·steps/s", "cores": threads, "kind": "oracle",
+            "sample": f"{wl.name} ({sample}); FP64 C oracle, {threads} threads, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step simulates a bounded sample of
+    the workload per scheme on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as ora
+    from oracle import quadrature
+
+    wl = _workload(args)
+    schemes = ["picard", "full"]
+    x, W = quadrature.rule_for(wl)
+    model = ora.OracleModel(wl, x, W)
+    threads = os.cpu_count() or 1
+    codes = {"picard": ora.PICARD, "full": ora.FULL}
+    per_step = args.ref_paths
+    for w in range(args.warmup):
+        for s in schemes:
+            ora.simulate(model, codes[s], path0=0, npaths=max(per_step // 8, threads), threads=threads)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        for s in schemes:
+            ora.simulate(model, codes[s], path0=k * per_step, npaths=per_step, threads=threads)
+    dt = time.perf_counter() - t0
+    units = args.steps * len(schemes) * per_step * wl.units_per_path()
+    val = units / dt
+    unit = "path·tenor·steps/s"
+    line = {"metric": METRIC, "value": val, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": _describe(wl, schemes), "reference_sample_paths_per_scheme": per_step},
+            "cpu_baseline": {"value": val, "unit": unit, "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} paths per scheme per step of {wl.name}"},
+            "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--paths", type=int, default=0, help="paths per GPU (default 2^20)")
+    ap.add_argument("--ref-paths", type=int, default=512, help="oracle paths per scheme per step")
+    ap.add_argument("--schemes", default="picard,full")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1006_3340_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1006_3340_gb300 import lll
+
+    wl = _workload(args)
+    schemes = [s for s in args.schemes.split(",") if s]
+    n, ns = wl.n, wl.strikes.shape[1]
+    first = rank * wl.paths
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    x, W = lll.lll_build_nig_quadrature(wl.alpha, wl.beta, wl.dbar, wl.a, wl.Q)
+    sims = {s: lll.LevyLibor(wl, x, W, stream=stream) for s in schemes}
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def one_step(evs=None):
+        for i, s in enumerate(schemes):
+            if evs is not None:
+                evs[i][0].record()
+            lll.lll_simulate(sims[s].ctx, lll.SCHEMES[s], first, wl.paths, wl.seed)
+            if evs is not None:
+                evs[i][1].record()
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    per_scheme_ms = {s: [] for s in schemes}
+    step_ms = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)  # L2 flush between timed steps (outside the events)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in schemes]
+        one_step(evs)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for i, s in enumerate(schemes):
+            ms = evs[i][0].elapsed_time(evs[i][1])
+            per_scheme_ms[s].append(ms)
+            tot += ms
+        step_ms.append(tot)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units_per_step = len(schemes) * wl.paths * wl.units_per_path() * world
+    value = units_per_step * args.steps / (total_ms * 1e-3)
+
+    # per-scheme throughput and caplet prices of the last step
+    per = {}
+    for s in schemes:
+        ms = statistics.mean(per_scheme_ms[s])
+        kms, _ = sims[s].kernel_ms()
+        p, se = sims[s].prices()
+        per[s] = {"units_per_s": wl.paths * wl.units_per_path() / (ms * 1e-3), "ms": ms,
+                  "path_kernel_ms_last": kms, "atm_price_T10y": float(p[n - 1, ns // 2])}
+    if "picard" in per and "full" in per:
+        pp, _ = sims["picard"].prices()
+        pf, _ = sims["full"].prices()
+        per["picard_vs_full_max_bp"] = float(np.abs(pp - pf).max() * 1e4)
+
+    # roofline of the dominant kernel: the quadrature sweep costs 3Q FP32
+    # lane-ops per unit (one FMA into A, one multiply w*E, one FMA into P)
+    dom = max(schemes, key=lambda s: statistics.mean(per_scheme_ms[s]))
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 128 * sm_max * 1e6 / 1e12
+    dom_ms = statistics.mean(per_scheme_ms[dom])
+    ops = wl.paths * wl.units_per_path() * 3 * wl.Q
+    achieved = ops / (dom_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFP32-lane-op/s",
+                "frac": achieved / peak, "traffic": None, "kernel": f"path_kernel<{dom}, QP={wl.Q}>",
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)"}
+    if clocks and clocks.get("sm_mhz"):
+        roofline["frac_at_sampled_clock"] = achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+
+    # end to end through the C ABI from host arrays: init (H2D of the model
+    # inputs, FP64 tables on the GPU), strikes, each scheme, prices (D2H).
+    e2e = None
+    if not args.no_e2e:
+        h2d = (wl.L0.nbytes + wl.lam.nbytes + x.nbytes + W.nbytes) * len(schemes) + wl.strikes.nbytes * len(schemes)
+        d2h = len(schemes) * 2 * n * ns * 8
+        ts = []
+        for k in range(max(2, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for s in schemes:
+                sim = lll.LevyLibor(wl, x, W, stream=stream)
+                lll.lll_simulate(sim.ctx, lll.SCHEMES[s], first, wl.paths, wl.seed)
+                sim.prices()
+                sim.close()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        et = statistics.mean(ts)
+        if world > 1:
+            t = torch.tensor([et], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            et = float(t.item())
+        e2e = {"value": units_per_step / et, "unit": "path·tenor·steps/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "note": "lll_init + lll_set_strikes + lll_simulate + lll_price_caplets + lll_destroy per scheme"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, schemes)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "path·tenor·steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": _describe(wl, schemes), "global_paths": wl.paths * world,
+                           "parallelism": f"path shards x{world}", "l2": "flushed between timed steps "
+                           f"({L2_FLUSH_BYTES >> 20} MiB write outside the events)"},
+                "per_scheme": per, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "clocks": clocks, "gpu_launches": 2 * len(schemes) * args.steps}
+        print(json.dumps(line), flush=True)
+    for s in sims.values():
+        s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

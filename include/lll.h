@@ -1,0 +1,154 @@
+/*
+ * lll.h -- C ABI of liblll.so: GB300 (sm_103a) Monte Carlo of the Levy LIBOR
+ * model under the terminal measure, after A. Papapantoleon and D. Skovmand,
+ * "Numerical Methods for the Levy LIBOR model" (arXiv 1006.3340).
+ *
+ * Conventions used by every call
+ * ------------------------------
+ *  - Tenor (Section 2): accrual dates T_k = k * delta, k = 0..N, terminal
+ *    date T_N = T_*.  The simulated rates are L_m = L(., T_m), m = 1..n with
+ *    n = N - 1 (the paper's N); L_0 is the spot rate, known at t = 0.
+ *  - Time grid: s Euler steps per accrual period, h = delta / s, t_k = k h,
+ *    k = 0..n*s-1.  Rate i is simulated while k < i*s (it fixes at T_i).
+ *  - All host arrays are row-major, owned by the caller, read during the
+ *    call only (inputs are copied into library-owned device memory).
+ *  - Every device buffer is allocated and owned by the library and is freed
+ *    by lll_destroy.  Work is issued on the stream given to lll_init (NULL =
+ *    the legacy default stream); calls returning host data synchronise it.
+ *  - Every function returns LLL_OK (0) or a negative status.  After an
+ *    error, lll_last_error(ctx) gives a message.  LLL_EDOMAIN from lll_init is
+ *    a warning: the context is created and usable.
+ */
+#ifndef LLL_H
+#define LLL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LLL_OK 0
+#define LLL_EINVAL (-1)      /* null pointer, bad size, NaN/Inf, L0 <= 0, delta <= 0, zero node */
+#define LLL_EDOMAIN (-2)     /* NIG sum |lambda| >= alpha - |beta| (LR1 fails for the untruncated
+                                measure; the compensator is truncated to the rule's range) */
+#define LLL_ECUDA (-3)       /* a CUDA runtime call failed; the message names it */
+#define LLL_ETIMEOUT (-4)    /* a bounded device-side wait gave up */
+#define LLL_ENOMEM (-5)      /* device or host allocation failed */
+#define LLL_ESTATE (-6)      /* call out of order (e.g. pricing before simulating) */
+#define LLL_EUNSUPPORTED (-7)/* size beyond what the compiled kernels handle (Q > 128) */
+
+/* Schemes.  LLL_FULL: the log-Euler scheme of Eq. (log-LIB-SDE-2) with the
+ * drift of Eq. (LIBOR-drift-PT) evaluated at the simulated later rates.
+ * LLL_PICARD: the drift of Eq. (bdrift), evaluated at the Picard iterate
+ * Z^(1) of Eq. (Picard-2) (Section 3.1).  LLL_FROZEN: L^0 = exp(Z^(1)), the
+ * frozen-drift approximation (Section 1, Section 3.2).  LLL_MLP: the full
+ * scheme with the jump compensator replaced by a trained network. */
+typedef enum { LLL_FULL = 0, LLL_PICARD = 1, LLL_MLP = 2, LLL_FROZEN = 3 } lll_scheme;
+
+/* Driver H (Section 2, Eq. (canon-LIBOR)).  LLL_DRIVER_NIG: pure-jump NIG
+ * (Section 4), drawn as beta V + sqrt(V) Z + mu h with V inverse Gaussian.
+ * LLL_DRIVER_BROWNIAN: H = W (c = 1, no jumps), the log-normal LIBOR model. */
+typedef enum { LLL_DRIVER_NIG = 0, LLL_DRIVER_BROWNIAN = 1 } lll_driver;
+
+/* NIG parameters (alpha, beta, delta-bar, mu) of H_1.  mu = NaN selects the
+ * martingale value -delta_bar * beta / sqrt(alpha^2 - beta^2), which makes H a
+ * martingale as Section 2 requires. */
+typedef struct {
+    double alpha, beta, delta, mu;
+} lll_nig;
+
+typedef struct lll_ctx lll_ctx;
+
+/* lll_init -- build a model context (Sections 2 and 4).
+ *   out        : receives the context (set to NULL on failure).
+ *   N          : accrual dates, N >= 2 (n = N-1 simulated rates), N <= 4096.
+ *   tenor_delta: accrual fraction delta > 0 (all periods equal).
+ *   L0         : [N] initial forward rates L(0, T_m), m = 0..N-1, all > 0
+ *                (Eq. (i-val) gives them from the bond curve).
+ *   steps_per_period: s >= 1.
+ *   lambda     : [n*s][n], lambda[k*n + (l-1)] = lambda(t_k, T_l), the
+ *                volatility of rate l at the left point of step k (LR1).
+ *   driver     : lll_driver.
+ *   nig        : NIG parameters (ignored for the Brownian driver); alpha > |beta|,
+ *                delta > 0.
+ *   Q, nodes, weights: quadrature of the Levy measure, Q in [1, 128]:
+ *                int g(x) F(dx) ~= sum_j weights[j] g(nodes[j]) / nodes[j]^2,
+ *                i.e. the weights integrate against x^2 nu(x) dx.  Nodes must be
+ *                finite and non-zero.  Ignored (may be NULL, Q = 0) for the
+ *                Brownian driver.
+ *   cuda_stream: cudaStream_t to issue all work on (NULL = default stream).
+ * Builds in FP64 on the GPU the per-step tables of the compensator integrand
+ * and the frozen-curve drift b(t_k, T_l; Z(0)) of Eq. (Picard-2) with its
+ * running integral.  Returns LLL_EDOMAIN (context usable) when
+ * max_k sum_l |lambda(t_k, T_l)| >= alpha - |beta|. */
+int lll_init(lll_ctx **out, int N, double tenor_delta, const double *L0, int steps_per_period,
+             const double *lambda, int driver, lll_nig nig, int Q, const double *nodes,
+             const double *weights, void *cuda_stream);
+
+/* lll_set_strikes -- strikes of the caplets of Eq. (caplet), needed before
+ * lll_simulate because payoffs are accumulated on the fly.
+ *   n_strikes: 1..64; strikes: [n][n_strikes], row m-1 = caplet fixing at T_m. */
+int lll_set_strikes(lll_ctx *ctx, int n_strikes, const double *strikes);
+
+/* lll_set_snapshots -- keep log L_l(T_m), l >= m, for `count` paths of each
+ * simulation (parity checks): the paths whose index relative to first_path is
+ * a multiple of `stride` (>= 1), the first `count` of them.  count = 0
+ * disables. */
+int lll_set_snapshots(lll_ctx *ctx, uint64_t count, uint64_t stride);
+
+/* lll_simulate -- simulate paths [first_path, first_path + paths) of one
+ * scheme and accumulate caplet payoff sums.  Path p draws its increments from
+ * Philox-4x32-10 with key (seed_lo, seed_hi) and counter (k, 0, p_lo, p_hi),
+ * so any path range reproduces the same paths (sharding, resumption).  Resets
+ * the accumulators.  Asynchronous on the context's stream.
+ * LLL_MLP requires lll_mlp_train or lll_mlp_load first (LLL_ESTATE). */
+int lll_simulate(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, uint64_t seed);
+
+/* lll_get_sums -- FP64 payoff sums of the last simulation, for merging shards
+ * in a fixed order: sum[n][n_strikes], sumsq[n][n_strikes], *count = paths.
+ * Synchronises the stream. */
+int lll_get_sums(lll_ctx *ctx, double *sum, double *sumsq, uint64_t *count);
+
+/* lll_price_caplets -- Eq. (caplet): price = mean payoff (already carries
+ * delta * B(0, T_N) and the numeraire product), stderr = sample standard
+ * deviation / sqrt(paths).  prices, stderr_: [n][n_strikes].  stderr_ may be
+ * NULL.  Synchronises the stream. */
+int lll_price_caplets(lll_ctx *ctx, double *prices, double *stderr_);
+
+/* lll_get_paths -- snapshots of the last simulation: out[(p*n + (m-1))*n +
+ * (l-1)] = log L_l(T_m) for l >= m (NaN for l < m), for recorded snapshots
+ * p in [first, first+count); recorded snapshot q is path first_path +
+ * q*stride.  Synchronises the stream. */
+int lll_get_paths(lll_ctx *ctx, uint64_t first, uint64_t count, float *out);
+
+/* lll_set_launch -- override the launch shape of the path kernels:
+ * threads per block (32..256, multiple of 32), resident blocks per SM
+ * (0 = occupancy maximum), table rows staged per pipeline chunk (>= 1).
+ * 0 for any argument keeps the library default. */
+int lll_set_launch(lll_ctx *ctx, int threads_per_block, int blocks_per_sm, int chunk_rows);
+
+/* lll_kernel_ms -- device time of the last simulation's path kernel and of the
+ * whole lll_simulate call, from CUDA events on the context's stream.
+ * Synchronises the stream. */
+int lll_kernel_ms(lll_ctx *ctx, float *path_kernel_ms, float *simulate_ms);
+
+/* lll_build_nig_quadrature -- Q-point Gauss rule of the weight x^2 nu(x) on
+ * [-xmax, xmax], nu the NIG Levy density (Barndorff-Nielsen 1997; the paper
+ * gives only kappa, Section 4).  Host computation in FP64.
+ *   nodes, weights: [Q] outputs, Q in [1, 128]. */
+int lll_build_nig_quadrature(lll_nig nig, double xmax, int Q, double *nodes, double *weights);
+
+/* lll_last_error -- message of the last failing call on ctx (ctx may be NULL:
+ * the last failure of lll_init or lll_build_nig_quadrature in this thread). */
+const char *lll_last_error(const lll_ctx *ctx);
+
+/* lll_destroy -- free the context and its device memory (NULL is a no-op). */
+void lll_destroy(lll_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LLL_H */

@@ -209,6 +209,7 @@ typedef struct {
     const oracle_pre *P;
     int scheme, ns;
     uint64_t seed, path0, npaths;
+    const uint64_t *plist; /* explicit path indices, or NULL for path0 + p */
     uint32_t inst;
     const double *strikes; /* [n][ns] */
     double *sum, *sumsq;   /* [n][ns], thread-local */
@@ -223,7 +224,7 @@ static void run_path(oracle_job *J, uint64_t p, double *Z, double *Y, double *w,
     const oracle_model *m = P->m;
     int n = P->n, s = m->s, S = P->S;
     double h = P->h, delta = m->delta;
-    uint64_t path = J->path0 + p;
+    uint64_t path = J->plist ? J->plist[p] : J->path0 + p;
     double mmin = INFINITY;
     for (int l = 0; l < n; ++l) { Z[l] = P->Z0[l]; Y[l] = 0.0; }
     for (int k = 0; k < S; ++k) {
@@ -283,9 +284,10 @@ static void *run_job(void *arg)
 /* Simulate paths [path0, path0 + npaths) of one scheme.  Sums of payoffs and */
 /* of squared payoffs per (maturity, strike) are accumulated per thread over */
 /* contiguous path blocks and merged in thread order.                        */
-int oracle_simulate(const oracle_model *m, int scheme, uint64_t seed, uint32_t inst,
-                    uint64_t path0, uint64_t npaths, int ns, const double *strikes,
-                    double *sum, double *sumsq, double *snap, double *min_margin, int nthreads)
+static int simulate_impl(const oracle_model *m, int scheme, uint64_t seed, uint32_t inst,
+                         uint64_t path0, const uint64_t *plist, uint64_t npaths, int ns,
+                         const double *strikes, double *sum, double *sumsq, double *snap,
+                         double *min_margin, int nthreads)
 {
     if (!m || m->N < 2 || m->s < 1 || m->Q < 0 || !(m->delta > 0)) return -1;
     if (scheme != ORACLE_FULL && scheme != ORACLE_PICARD && scheme != ORACLE_FROZEN) return -1;
@@ -304,6 +306,7 @@ int oracle_simulate(const oracle_model *m, int scheme, uint64_t seed, uint32_t i
         oracle_job *J = &jobs[t];
         J->P = &P; J->scheme = scheme; J->ns = ns; J->seed = seed; J->inst = inst;
         J->path0 = path0 + start; J->npaths = cnt; J->strikes = strikes;
+        J->plist = plist ? plist + start : NULL;
         J->sum = acc + (size_t)2 * t * n * ns;
         J->sumsq = J->sum + (size_t)n * ns;
         J->snap = snap ? snap + (size_t)start * n * n : NULL;
@@ -322,6 +325,23 @@ int oracle_simulate(const oracle_model *m, int scheme, uint64_t seed, uint32_t i
     free(jobs); free(th); free(acc);
     pre_free(&P);
     return status;
+}
+
+int oracle_simulate(const oracle_model *m, int scheme, uint64_t seed, uint32_t inst,
+                    uint64_t path0, uint64_t npaths, int ns, const double *strikes,
+                    double *sum, double *sumsq, double *snap, double *min_margin, int nthreads)
+{
+    return simulate_impl(m, scheme, seed, inst, path0, NULL, npaths, ns, strikes, sum, sumsq, snap,
+                         min_margin, nthreads);
+}
+
+/* Same, for an explicit list of path indices (sampled paths of a large run). */
+int oracle_simulate_list(const oracle_model *m, int scheme, uint64_t seed, uint32_t inst,
+                         const uint64_t *paths, uint64_t npaths, int ns, const double *strikes,
+                         double *sum, double *sumsq, double *snap, double *min_margin, int nthreads)
+{
+    return simulate_impl(m, scheme, seed, inst, 0, paths, npaths, ns, strikes, sum, sumsq, snap,
+                         min_margin, nthreads);
 }
 
 /* Driver increments for paths [path0, path0+npaths) and all n*s steps:     */

@@ -50,6 +50,7 @@ def _load():
     if _lib is None:
         _lib = ctypes.CDLL(build())
         _lib.oracle_simulate.restype = ctypes.c_int
+        _lib.oracle_simulate_list.restype = ctypes.c_int
         _lib.oracle_increments.restype = ctypes.c_int
         _lib.oracle_drift.restype = ctypes.c_int
         _lib.oracle_frozen_drift.restype = ctypes.c_int
@@ -113,6 +114,33 @@ def simulate(model: OracleModel, scheme: int, path0: int = 0, npaths: Optional[i
         raise RuntimeError(f"oracle_simulate failed: {st}")
     return dict(sum=s1, sumsq=s2, snap=snap, min_margin=mm, npaths=npaths,
                 **moments(s1, s2, npaths))
+
+
+def simulate_paths(model: OracleModel, scheme: int, paths, strikes=None, threads=None,
+                   seed=None, inst=None):
+    """Like :func:`simulate` for an explicit list of path indices; returns the
+    snapshots snap[q, m-1, l-1] of path paths[q] and the payoff sums."""
+    lib = _load()
+    wl = model.wl
+    n = model.n
+    plist = np.ascontiguousarray(paths, dtype=np.uint64)
+    npaths = len(plist)
+    strikes = np.ascontiguousarray(wl.strikes if strikes is None else strikes, dtype=np.float64)
+    ns = strikes.shape[1]
+    s1 = np.zeros((n, ns))
+    s2 = np.zeros((n, ns))
+    snap = np.full((npaths, n, n), np.nan)
+    mm = np.zeros(npaths)
+    threads = threads or os.cpu_count() or 1
+    seed = wl.seed if seed is None else seed
+    inst = wl.inst if inst is None else inst
+    st = lib.oracle_simulate_list(ctypes.byref(model.c), ctypes.c_int(scheme), ctypes.c_uint64(seed),
+                                  ctypes.c_uint32(inst), plist.ctypes.data_as(ctypes.c_void_p),
+                                  ctypes.c_uint64(npaths), ctypes.c_int(ns), _ptr(strikes), _ptr(s1),
+                                  _ptr(s2), _ptr(snap), _ptr(mm), ctypes.c_int(threads))
+    if st != 0:
+        raise RuntimeError(f"oracle_simulate_list failed: {st}")
+    return dict(sum=s1, sumsq=s2, snap=snap, min_margin=mm, npaths=npaths)
 
 
 def moments(s1, s2, npaths):

@@ -1,0 +1,56 @@
+// lll_internal.h -- structures shared by the translation units of liblll.so.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace lll {
+
+enum Scheme { FULL = 0, PICARD = 1, MLP = 2, FROZEN = 3 };
+
+// Largest padded node count the path kernels are compiled for.
+constexpr int kMaxQP = 128;
+// Maximum threads per block of the path kernels.
+constexpr int kMaxThreads = 256;
+
+// Arguments of the path kernels (one simulation of one scheme).
+struct PathArgs {
+    const float4 *tab;    // [S][n][QP/2]: (E_j, E_j+1, a_j, a_j+1), E = e^{lambda x_j}-1, a = W_j E / x_j^2
+    const float4 *row;    // [S][n]: (lambda_l(t_k), K_l(k), D0_l(t_k), b0_l(t_k) * h)
+    const float *Z0;      // [n]: log L(0, T_l)
+    const float *c0;      // [n]: log L(0, T_l) + log delta
+    const float *strikes; // [n][ns]
+    double *partials;     // [grid][n][ns][2]: per-block payoff sum and sum of squares
+    float *state;         // [grid][nst][n][threads]: per-path state (log-rate offsets)
+    float *snap;          // [n][n][n_snap]: log L_l(T_m) for the first n_snap paths, or null
+    uint64_t n_snap, snap_stride, snap_pitch; // recorded paths, path stride, row pitch of snap
+    uint64_t first_path, paths;
+    int n, s, S, ns, chunk_rows;
+    uint32_t key0, key1, inst;
+    int driver;           // 0 NIG, 1 Brownian
+    float h, sqrt_h, delta, dBN; // dBN = delta * B(0, T_N)
+    // NIG increment over one step: IG(mean m, shape l) mixing variable.
+    float ig_m, ig_m2, ig_hl, ig_fl; // m, m^2, m / (2 l), 4 m l
+    float nig_beta, nig_muh;         // beta, mu * h
+    double ig_md, ig_ld;             // m and l in FP64 for the acceptance re-check
+};
+
+// Launchers implemented in lll_paths.cu.  Return a cudaError_t value.
+int launch_path_kernel(int scheme, int QP, int grid, int threads, size_t smem, cudaStream_t st,
+                       const PathArgs &a);
+int path_kernel_occupancy(int scheme, int QP, int threads, size_t smem, int *blocks_per_sm);
+int path_kernel_prepare(int scheme, int QP, size_t smem);
+bool path_kernel_supported(int scheme, int QP);
+size_t path_kernel_smem(int QP, int n, int ns, int threads, int chunk_rows);
+
+// Launchers implemented in lll_tables.cu.
+int launch_tables(const double *lam, const double *x, const double *W, int n, int S, int Q, int QP,
+                  float4 *tab, float4 *row, cudaStream_t st);
+int launch_frozen_drift(const double *lam, const double *x, const double *W, const double *w0,
+                        int n, int S, int Q, double c, double h, double *b0, float4 *row,
+                        cudaStream_t st);
+int launch_finalize(const double *partials, int grid, int n_out, double *sums, cudaStream_t st);
+
+}  // namespace lll

@@ -1,0 +1,335 @@
+// lll_paths.cu -- the Monte Carlo path kernels (full Euler, Picard, frozen drift).
+//
+// One thread carries one path through all n*s Euler steps of Eq. (log-LIB-SDE-2)
+// (Section 3).  Per step k it draws the shared increment Delta H_k and sweeps
+// the live rates i = n .. i_min (rate i lives while k < i*s), carrying, for
+// every quadrature node x_j, the running product
+//     P_j = prod_{l > i} (1 + w_l (e^{lambda_l x_j} - 1))
+// of the beta factors of Eq. (Levy-LIBOR-beta).  The jump part of the drift of
+// Eq. (LIBOR-drift-PT) is then
+//     A_i = int [(e^{lambda_i x}-1) prod_{l>i} beta_l - lambda_i x] F(dx)
+//         = K_i + sum_j a_ij P_j,
+// with a_ij = W_j (e^{lambda_i x_j}-1) / x_j^2 and K_i = C_i - sum_j a_ij,
+// C_i = sum_j W_j (e^{lambda_i x_j} - 1 - lambda_i x_j) / x_j^2 (both from FP64
+// tables).  The sweep costs 3 FP32 operations per (node, live rate): one FMA
+// into A_i, one multiply w_i E_ij and one FMA into P_j (packed as f32x2).
+//
+//  * FULL   (Eq. (LIBOR-drift-PT)): w_l from the simulated Z_l(t_k).
+//  * PICARD (Eq. (bdrift)):         w_l from Z^(1)_l(t_k) = Z_l(0) + D0_l(t_k)
+//                                   + int_0^{t_k} lambda_l dH (Eq. (Picard-2)),
+//                                   which depends on the H path only.
+//  * FROZEN:                        L^0 = exp(Z^(1)): the drift is b(t_k; Z(0)).
+//  * Brownian driver (no quadrature): b_i = -lambda_i^2/2 - lambda_i sum_{l>i} w_l lambda_l.
+//
+// At T_m (end of step m*s-1) the caplet payoff of Eq. (caplet),
+//     delta B(0,T_N) prod_{l>m} (1 + delta L_l(T_m)) (L_m(T_m) - K)^+,
+// is reduced over the block (warp shuffles, then warps in fixed order) into
+// FP64 Kahan accumulators; per-block partials are summed in fixed order by a
+// second kernel, so results are run-to-run deterministic.
+//
+// Layout: the per-step table rows (k, i) of the live rates are staged into
+// shared memory in chunks of chunk_rows rows by cp.async, double-buffered so
+// the next chunk loads while the current one is swept.  Every thread of a
+// block is at the same (k, i), so table reads are shared-memory broadcasts.
+// Path state (offsets of log L from log L(0)) lives in a per-block global
+// scratch slot [nst][n][threads] that stays L1/L2 resident; the grid is
+// persistent (one wave of resident blocks looping over path tiles).
+#include <cuda_runtime.h>
+
+#include "lll_device.cuh"
+#include "lll_internal.h"
+
+namespace lll {
+namespace {
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ void kahan_add(double *s, double *c, double x)
+{
+    const double y = x - *c;
+    const double t = *s + y;
+    *c = (t - *s) - y;
+    *s = t;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct Smem {
+    float4 *tab;  // [2][CH * QP/2]
+    float4 *row;  // [2][CH]
+    float *c0;    // [n]
+    double *bsum; // [n * ns][4]: sum, comp, sumsq, comp
+    double *red;  // [warps][ns][2]
+};
+
+__host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
+
+__host__ __device__ inline size_t smem_bytes(int QP, int n, int ns, int threads, int CH)
+{
+    size_t b = 0;
+    b += align16(sizeof(float4) * 2 * (size_t)CH * (QP / 2));
+    b += align16(sizeof(float4) * 2 * (size_t)CH);
+    b += align16(sizeof(float) * (size_t)n);
+    b += align16(sizeof(double) * 4 * (size_t)n * ns);
+    b += align16(sizeof(double) * 2 * (size_t)(threads / 32) * ns);
+    return b;
+}
+
+__device__ inline Smem carve(unsigned char *base, int QP, int n, int ns, int threads, int CH)
+{
+    Smem s;
+    size_t o = 0;
+    s.tab = reinterpret_cast<float4 *>(base + o);
+    o += align16(sizeof(float4) * 2 * (size_t)CH * (QP / 2));
+    s.row = reinterpret_cast<float4 *>(base + o);
+    o += align16(sizeof(float4) * 2 * (size_t)CH);
+    s.c0 = reinterpret_cast<float *>(base + o);
+    o += align16(sizeof(float) * (size_t)n);
+    s.bsum = reinterpret_cast<double *>(base + o);
+    o += align16(sizeof(double) * 4 * (size_t)n * ns);
+    s.red = reinterpret_cast<double *>(base + o);
+    return s;
+}
+
+// Stage the table rows of chunk c of step k (rates i in [ibot, itop]) into buffer b.
+template <int QP>
+__device__ __forceinline__ void issue_chunk(const PathArgs &a, const Smem &sm, int k, int c, int b)
+{
+    const int n = a.n, CH = a.chunk_rows;
+    const int imin = k / a.s + 1;
+    const int itop = n - c * CH;
+    const int ibot = max(imin, itop - CH + 1);
+    const int cnt = itop - ibot + 1;
+    const size_t r0 = (size_t)k * n + (ibot - 1);
+    if (QP > 0) {
+        constexpr int Q2 = QP / 2;
+        const float4 *src = a.tab + r0 * Q2;
+        float4 *dst = sm.tab + (size_t)b * CH * Q2;
+        for (int e = threadIdx.x; e < cnt * Q2; e += blockDim.x) cp_async16(dst + e, src + e);
+    }
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) cp_async16(sm.row + b * CH + e, a.row + r0 + e);
+}
+
+template <int SCHEME, int QP>
+__global__ void __launch_bounds__(kMaxThreads) path_kernel(const PathArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int Q2 = QP > 0 ? QP / 2 : 1;
+    constexpr int NST = (SCHEME == PICARD) ? 2 : 1;
+    const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = a.n, s = a.s, S = a.S, ns = a.ns, CH = a.chunk_rows;
+    const Smem sm = carve(smem_raw, QP, n, ns, T, CH);
+
+    for (int e = tid; e < n; e += T) sm.c0[e] = a.c0[e];
+    for (int e = tid; e < 4 * n * ns; e += T) sm.bsum[e] = 0.0;
+
+    float *st = a.state + (size_t)blockIdx.x * NST * n * T + tid;
+    const uint64_t ntiles = (a.paths + T - 1) / T;
+    const float h = a.h, delta = a.delta;
+
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint64_t lp = tile * (uint64_t)T + tid; // path index within this simulation
+        const bool active = lp < a.paths;
+        const uint64_t p = a.first_path + lp;
+        uint64_t sidx = ~0ull; // snapshot slot of this path, if it is recorded
+        if (a.snap != nullptr && active && lp % a.snap_stride == 0 && lp / a.snap_stride < a.n_snap)
+            sidx = lp / a.snap_stride;
+        for (int l = 0; l < NST * n; ++l) st[(size_t)l * T] = 0.0f;
+
+        __syncthreads(); // previous tile's readers of both buffers are done
+        issue_chunk<QP>(a, sm, 0, 0, 0);
+        cp_commit();
+        int buf = 0;
+
+        for (int k = 0; k < S; ++k) {
+            const int imin = k / s + 1;
+            const int nch = (n - imin + CH) / CH; // ceil((n - imin + 1) / CH)
+            const bool mat = (k + 1) % s == 0;     // rate imin fixes at t_{k+1} = T_imin
+            const float dH = draw_increment(a, p, (uint32_t)k);
+
+            float2 P[Q2];
+#pragma unroll
+            for (int j = 0; j < Q2; ++j) P[j] = make_float2(1.0f, 1.0f);
+            float scont = 0.0f, num = 1.0f, Lm = 0.0f;
+
+            for (int c = 0; c < nch; ++c) {
+                int nk = k, nc = c + 1;
+                if (nc == nch) { nk = k + 1; nc = 0; }
+                if (nk < S) issue_chunk<QP>(a, sm, nk, nc, buf ^ 1);
+                cp_commit();
+                cp_wait_1();
+                __syncthreads();
+
+                const int itop = n - c * CH;
+                const int ibot = max(imin, itop - CH + 1);
+                const float4 *tb = sm.tab + (size_t)buf * CH * Q2;
+                const float4 *rb = sm.row + buf * CH;
+                for (int i = itop; i >= ibot; --i) {
+                    const int r = i - ibot;
+                    const float4 rc = rb[r]; // lambda, K, D0, b0*h
+                    float *sp = st + (size_t)(i - 1) * T;
+                    float v0 = sp[0];
+                    float v1 = (NST == 2) ? sp[(size_t)n * T] : 0.0f;
+                    float bh;
+                    if (SCHEME == FROZEN) {
+                        bh = rc.w;
+                    } else {
+                        const float zoff = (SCHEME == FULL) ? v0 : (rc.z + v0);
+                        const float x = sm.c0[i - 1] + zoff; // log(delta L) at t_k
+                        const float w = __frcp_rn(1.0f + __expf(-x)); // delta L / (1 + delta L)
+                        float b;
+                        if (QP > 0) {
+                            const float4 *tr = tb + (size_t)r * Q2;
+                            float2 acc[4];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.0f, 0.0f);
+                            const float2 w2 = make_float2(w, w);
+#pragma unroll
+                            for (int j = 0; j < Q2; ++j) {
+                                const float4 v = tr[j];
+                                const float2 e2 = make_float2(v.x, v.y);
+                                const float2 a2 = make_float2(v.z, v.w);
+                                acc[j & 3] = __ffma2_rn(a2, P[j], acc[j & 3]);
+                                P[j] = __ffma2_rn(__fmul2_rn(w2, e2), P[j], P[j]);
+                            }
+                            const float Ai = rc.y + (((acc[0].x + acc[0].y) + (acc[1].x + acc[1].y)) +
+                                                     ((acc[2].x + acc[2].y) + (acc[3].x + acc[3].y)));
+                            b = -Ai;
+                        } else {
+                            b = -0.5f * rc.x * rc.x - rc.x * scont;
+                            scont = fmaf(w, rc.x, scont);
+                        }
+                        bh = b * h;
+                    }
+                    float znew;
+                    if (SCHEME == PICARD) {
+                        v0 = fmaf(rc.x, dH, v0); // int lambda dH
+                        v1 += bh;                // Picard drift integral
+                        sp[0] = v0;
+                        sp[(size_t)n * T] = v1;
+                        znew = v0 + v1;
+                    } else {
+                        v0 += fmaf(rc.x, dH, bh);
+                        sp[0] = v0;
+                        znew = v0;
+                    }
+                    if (mat) {
+                        znew += a.Z0[i - 1];
+                        if (i > imin) num *= fmaf(delta, expf(znew), 1.0f);
+                        else Lm = expf(znew);
+                        if (sidx != ~0ull)
+                            a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = znew;
+                    }
+                }
+                __syncthreads();
+                buf ^= 1;
+            }
+
+            if (mat) {
+                const int m = imin;
+                for (int q = 0; q < ns; ++q) {
+                    const float K = a.strikes[(size_t)(m - 1) * ns + q];
+                    const double pay = active ? (double)(a.dBN * num * fmaxf(Lm - K, 0.0f)) : 0.0;
+                    const double s1 = warp_sum(pay);
+                    const double s2 = warp_sum(pay * pay);
+                    if (lane == 0) {
+                        sm.red[((size_t)warp * ns + q) * 2 + 0] = s1;
+                        sm.red[((size_t)warp * ns + q) * 2 + 1] = s2;
+                    }
+                }
+                __syncthreads();
+                if (tid < ns) {
+                    double s1 = 0.0, s2 = 0.0;
+                    for (int wv = 0; wv < (T >> 5); ++wv) {
+                        s1 += sm.red[((size_t)wv * ns + tid) * 2 + 0];
+                        s2 += sm.red[((size_t)wv * ns + tid) * 2 + 1];
+                    }
+                    double *acc = sm.bsum + 4 * ((size_t)(m - 1) * ns + tid);
+                    kahan_add(acc + 0, acc + 1, s1);
+                    kahan_add(acc + 2, acc + 3, s2);
+                }
+                __syncthreads();
+            }
+        }
+        cp_wait_0();
+    }
+    __syncthreads();
+    double *out = a.partials + (size_t)blockIdx.x * n * ns * 2;
+    for (int e = tid; e < n * ns; e += T) {
+        out[2 * e + 0] = sm.bsum[4 * e + 0];
+        out[2 * e + 1] = sm.bsum[4 * e + 2];
+    }
+}
+
+typedef void (*KernelFn)(const PathArgs);
+
+template <int SCHEME>
+KernelFn pick_qp(int QP)
+{
+    switch (QP) {
+    case 0: return path_kernel<SCHEME, 0>;
+    case 16: return path_kernel<SCHEME, 16>;
+    case 32: return path_kernel<SCHEME, 32>;
+    case 64: return path_kernel<SCHEME, 64>;
+    case 96: return path_kernel<SCHEME, 96>;
+    case 128: return path_kernel<SCHEME, 128>;
+    default: return nullptr;
+    }
+}
+
+KernelFn pick(int scheme, int QP)
+{
+    switch (scheme) {
+    case FULL: return pick_qp<FULL>(QP);
+    case PICARD: return pick_qp<PICARD>(QP);
+    case FROZEN: return path_kernel<FROZEN, 0>;
+    default: return nullptr;
+    }
+}
+
+}  // namespace
+
+bool path_kernel_supported(int scheme, int QP) { return pick(scheme, QP) != nullptr; }
+
+size_t path_kernel_smem(int QP, int n, int ns, int threads, int chunk_rows)
+{
+    return smem_bytes(QP, n, ns, threads, chunk_rows);
+}
+
+int path_kernel_prepare(int scheme, int QP, size_t smem)
+{
+    KernelFn f = pick(scheme, QP);
+    if (!f) return (int)cudaErrorInvalidValue;
+    return (int)cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+int path_kernel_occupancy(int scheme, int QP, int threads, size_t smem, int *blocks_per_sm)
+{
+    KernelFn f = pick(scheme, QP);
+    if (!f) return (int)cudaErrorInvalidValue;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, smem);
+}
+
+int launch_path_kernel(int scheme, int QP, int grid, int threads, size_t smem, cudaStream_t st,
+                       const PathArgs &a)
+{
+    KernelFn f = pick(scheme, QP);
+    if (!f) return (int)cudaErrorInvalidValue;
+    // The frozen kernel stages no node table; its QP argument is ignored.
+    f<<<grid, threads, smem, st>>>(a);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace lll

@@ -1,0 +1,233 @@
+"""ctypes binding of liblll.so (include/lll.h).  Argument marshalling only:
+every step of the simulation runs in the library's CUDA kernels.
+
+The library must have been built (``paper_1006_3340_gb300.build.build()`` or
+``__graft_entry__.build()``); loading fails loudly otherwise.  There is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+LLL_OK, LLL_EINVAL, LLL_EDOMAIN, LLL_ECUDA, LLL_ETIMEOUT, LLL_ENOMEM, LLL_ESTATE, LLL_EUNSUPPORTED = \
+    0, -1, -2, -3, -4, -5, -6, -7
+LLL_FULL, LLL_PICARD, LLL_MLP, LLL_FROZEN = 0, 1, 2, 3
+LLL_DRIVER_NIG, LLL_DRIVER_BROWNIAN = 0, 1
+SCHEMES = {"full": LLL_FULL, "picard": LLL_PICARD, "mlp": LLL_MLP, "frozen": LLL_FROZEN}
+
+
+class LLLError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"liblll status {code}: {msg}")
+        self.code = code
+
+
+class lll_nig(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("delta", ctypes.c_double), ("mu", ctypes.c_double)]
+
+
+_lib = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load liblll.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"liblll.so not built ({path}); run paper_1006_3340_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    V, I, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64
+    sigs = {
+        "lll_init": (I, [ctypes.POINTER(V), I, ctypes.c_double, _dp, I, _dp, I, lll_nig, I, _dp, _dp, V]),
+        "lll_set_strikes": (I, [V, I, _dp]),
+        "lll_set_snapshots": (I, [V, U64, U64]),
+        "lll_simulate": (I, [V, I, U64, U64, U64]),
+        "lll_get_sums": (I, [V, _dp, _dp, ctypes.POINTER(U64)]),
+        "lll_price_caplets": (I, [V, _dp, _dp]),
+        "lll_get_paths": (I, [V, U64, U64, _fp]),
+        "lll_set_launch": (I, [V, I, I, I]),
+        "lll_kernel_ms": (I, [V, _fp, _fp]),
+        "lll_build_nig_quadrature": (I, [lll_nig, ctypes.c_double, I, _dp, _dp]),
+        "lll_last_error": (ctypes.c_char_p, [V]),
+        "lll_destroy": (None, [V]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _d(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(rc, ctx=None, allow=(LLL_OK,)):
+    if rc not in allow:
+        msg = load().lll_last_error(ctx)
+        raise LLLError(rc, msg.decode() if msg else "")
+    return rc
+
+
+# ---- the C entry points, same names ----------------------------------------
+def lll_build_nig_quadrature(alpha, beta, delta, xmax, Q, mu=float("nan")):
+    lib = load()
+    x = np.zeros(Q)
+    w = np.zeros(Q)
+    _check(lib.lll_build_nig_quadrature(lll_nig(alpha, beta, delta, mu), float(xmax), int(Q), _d(x), _d(w)))
+    return x, w
+
+
+def lll_init(N, delta, L0, s, lam, driver, nig=(0.0, 0.0, 0.0, float("nan")), nodes=None,
+             weights=None, stream: int = 0, allow_domain_warning: bool = True):
+    """Returns (ctx handle, status).  ``stream`` is a cudaStream_t as int."""
+    lib = load()
+    L0 = _f64(L0)
+    lam = _f64(lam)
+    if nodes is None:
+        nodes, weights, Q = np.zeros(1), np.zeros(1), 0
+    else:
+        nodes, weights = _f64(nodes), _f64(weights)
+        Q = len(nodes)
+    ctx = ctypes.c_void_p()
+    mu = float("nan") if nig[3] is None else float(nig[3])
+    rc = lib.lll_init(ctypes.byref(ctx), int(N), float(delta), _d(L0), int(s), _d(lam), int(driver),
+                      lll_nig(float(nig[0]), float(nig[1]), float(nig[2]), mu), int(Q), _d(nodes),
+                      _d(weights), ctypes.c_void_p(stream or None))
+    allowed = (LLL_OK, LLL_EDOMAIN) if allow_domain_warning else (LLL_OK,)
+    _check(rc, None, allowed)
+    return ctx, rc
+
+
+def lll_set_strikes(ctx, strikes):
+    strikes = _f64(strikes)
+    _check(load().lll_set_strikes(ctx, int(strikes.shape[1]), _d(strikes)), ctx)
+
+
+def lll_set_snapshots(ctx, count, stride=1):
+    _check(load().lll_set_snapshots(ctx, int(count), int(stride)), ctx)
+
+
+def lll_simulate(ctx, scheme, first_path, paths, seed):
+    _check(load().lll_simulate(ctx, int(scheme), int(first_path), int(paths), int(seed)), ctx)
+
+
+def lll_get_sums(ctx, n, ns):
+    s1 = np.zeros((n, ns))
+    s2 = np.zeros((n, ns))
+    cnt = ctypes.c_uint64()
+    _check(load().lll_get_sums(ctx, _d(s1), _d(s2), ctypes.byref(cnt)), ctx)
+    return s1, s2, cnt.value
+
+
+def lll_price_caplets(ctx, n, ns):
+    p = np.zeros((n, ns))
+    se = np.zeros((n, ns))
+    _check(load().lll_price_caplets(ctx, _d(p), _d(se)), ctx)
+    return p, se
+
+
+def lll_get_paths(ctx, n, first, count):
+    out = np.zeros((count, n, n), dtype=np.float32)
+    _check(load().lll_get_paths(ctx, int(first), int(count), out.ctypes.data_as(_fp)), ctx)
+    return out
+
+
+def lll_set_launch(ctx, threads=0, blocks_per_sm=0, chunk_rows=0):
+    _check(load().lll_set_launch(ctx, int(threads), int(blocks_per_sm), int(chunk_rows)), ctx)
+
+
+def lll_kernel_ms(ctx):
+    a = ctypes.c_float()
+    b = ctypes.c_float()
+    _check(load().lll_kernel_ms(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
+    return a.value, b.value
+
+
+def lll_last_error(ctx=None) -> str:
+    msg = load().lll_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def lll_destroy(ctx):
+    if ctx:
+        load().lll_destroy(ctx)
+
+
+# ---- convenience wrapper ---------------------------------------------------
+class LevyLibor:
+    """One model context (a workload from :mod:`workloads`) on the current CUDA
+    device and a caller-chosen stream."""
+
+    def __init__(self, wl, nodes=None, weights=None, stream: int = 0):
+        self.wl = wl
+        self.n = wl.n
+        if wl.driver == "nig":
+            if nodes is None:
+                nodes, weights = lll_build_nig_quadrature(wl.alpha, wl.beta, wl.dbar, wl.a, wl.Q)
+            drv = LLL_DRIVER_NIG
+            nig = (wl.alpha, wl.beta, wl.dbar, float("nan") if wl.mu is None else wl.mu)
+        else:
+            drv, nig, nodes, weights = LLL_DRIVER_BROWNIAN, (0.0, 0.0, 0.0, float("nan")), None, None
+        self.ctx, self.init_status = lll_init(wl.N, wl.delta, wl.L0, wl.s, wl.lam, drv, nig, nodes,
+                                              weights, stream)
+        self.ns = wl.strikes.shape[1]
+        lll_set_strikes(self.ctx, wl.strikes)
+
+    def set_strikes(self, strikes):
+        lll_set_strikes(self.ctx, strikes)
+        self.ns = np.asarray(strikes).shape[1]
+
+    def simulate(self, scheme="picard", paths=None, first_path=0, seed=None, snapshots=0,
+                 snapshot_stride=1):
+        sch = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+        lll_set_snapshots(self.ctx, snapshots, snapshot_stride)
+        lll_simulate(self.ctx, sch, first_path, self.wl.paths if paths is None else paths,
+                     self.wl.seed if seed is None else seed)
+
+    def prices(self):
+        return lll_price_caplets(self.ctx, self.n, self.ns)
+
+    def sums(self):
+        return lll_get_sums(self.ctx, self.n, self.ns)
+
+    def paths(self, first, count):
+        return lll_get_paths(self.ctx, self.n, first, count)
+
+    def kernel_ms(self):
+        return lll_kernel_ms(self.ctx)
+
+    def set_launch(self, threads=0, blocks_per_sm=0, chunk_rows=0):
+        lll_set_launch(self.ctx, threads, blocks_per_sm, chunk_rows)
+
+    def close(self):
+        if self.ctx:
+            lll_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

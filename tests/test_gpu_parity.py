@@ -1,0 +1,93 @@
+"""GPU (liblll.so, through the C ABI) against the FP64 oracle on the same
+seeded inputs and the same Philox streams.
+
+Bar (from the arithmetic): FP32 path state over <= 476 Euler steps keeps
+log-rates within ~1e-6 of FP64, so every recorded rate L_l(T_m) must agree to
+1e-5 relative; caplet prices (notional 1) to 1e-7 absolute.  The IG
+acceptance decision is taken in FP64 on both sides near its threshold, so no
+path is excluded; the oracle's smallest margin is reported.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as ora
+from oracle import quadrature
+from paper_1006_3340_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+REL_RATE = 1e-5
+ABS_PRICE = 1e-7
+SCHEMES = {"full": ora.FULL, "picard": ora.PICARD, "frozen": ora.FROZEN}
+
+
+@pytest.fixture(scope="module")
+def lll():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    from paper_1006_3340_gb300 import lll as mod
+
+    mod.load()
+    return mod
+
+
+def _compare(lll, wl, scheme, npaths, launch=None, x=None, W=None):
+    if x is None:
+        x, W = quadrature.rule_for(wl)
+    sim = lll.LevyLibor(wl, x, W)
+    try:
+        if launch:
+            sim.set_launch(*launch)
+        sim.simulate(scheme, paths=npaths, snapshots=npaths)
+        zg = sim.paths(0, npaths).astype(np.float64)
+        pg, seg = sim.prices()
+    finally:
+        sim.close()
+    ref = ora.simulate(ora.OracleModel(wl, x, W), SCHEMES[scheme], npaths=npaths, want_snap=True)
+    mask = ~np.isnan(ref["snap"])
+    assert np.array_equal(mask, ~np.isnan(zg))
+    rel = np.abs(np.expm1(zg[mask] - ref["snap"][mask]))
+    assert rel.max() <= REL_RATE, (scheme, rel.max())
+    dp = np.abs(pg - ref["price"])
+    assert dp.max() <= ABS_PRICE, (scheme, dp.max())
+    assert np.allclose(seg, ref["se"], rtol=1e-3, atol=1e-9)
+    return rel.max(), dp.max(), ref["min_margin"].min()
+
+
+@pytest.mark.parametrize("scheme", ["full", "picard", "frozen"])
+def test_small_plain(lll, scheme):
+    wl = workloads.small_plain(paths=4000)  # 31.25 blocks of 128: ragged last tile
+    _compare(lll, wl, scheme, 4000)
+
+
+@pytest.mark.parametrize("scheme", ["full", "picard"])
+def test_small_plain_brownian(lll, scheme):
+    wl = workloads.small_plain(paths=3000, driver="brownian")
+    _compare(lll, wl, scheme, 3000)
+
+
+@pytest.mark.parametrize("scheme", ["full", "picard", "frozen"])
+def test_large_single_subset(lll, scheme):
+    wl = workloads.large_single()
+    _compare(lll, wl, scheme, 2048 + 37)
+
+
+@pytest.mark.parametrize("scheme", ["full", "picard"])
+def test_long_dated_subset(lll, scheme):
+    wl = workloads.long_dated()
+    _compare(lll, wl, scheme, 200)
+
+
+@pytest.mark.parametrize("N,s,Q,paths", [(2, 1, 8, 1), (3, 2, 8, 33), (5, 3, 20, 200), (7, 4, 40, 129)])
+@pytest.mark.parametrize("scheme", ["full", "picard", "frozen"])
+def test_tiny_edge_shapes(lll, N, s, Q, paths, scheme):
+    wl = workloads.tiny(N=N, s=s, Q=Q, paths=paths)
+    _compare(lll, wl, scheme, paths)
+
+
+@pytest.mark.parametrize("launch", [(32, 0, 1), (64, 1, 2), (256, 0, 3), (96, 2, 0)])
+def test_launch_shapes_agree(lll, launch):
+    wl = workloads.large_single()
+    _compare(lll, wl, "picard", 300, launch=launch)
