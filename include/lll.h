@@ -134,6 +134,29 @@ int lll_set_launch(lll_ctx *ctx, int threads_per_block, int blocks_per_sm, int c
  * Synchronises the stream. */
 int lll_kernel_ms(lll_ctx *ctx, float *path_kernel_ms, float *simulate_ms);
 
+/* lll_simulate_noalloc -- lll_simulate for callers that must not allocate
+ * device memory once they are running: services that reserve all their device
+ * memory at start-up through their own pool, and latency-bound callers that
+ * cannot afford the device-wide synchronisation cudaMalloc / cudaFree may
+ * imply.  (The paper has no counterpart: this is an engineering entry point.)
+ *   ctx, scheme, first_path, paths, seed: as for lll_simulate (snapshots are
+ *                not recorded).
+ *   d_sums     : caller-owned device buffer of n * n_strikes * 2 doubles,
+ *                d_sums[2*(m*n_strikes + q)] = sum of payoffs and [... + 1] =
+ *                sum of squared payoffs of maturity m+1, strike q.
+ * Makes the same launch as lll_simulate, so the sums equal lll_get_sums'.
+ * Scratch (per-block path state and payoff partials) comes from one static
+ * 32 MiB device array that every GPU loading the library holds until exit;
+ * a launch needing more returns LLL_EUNSUPPORTED with the byte counts in
+ * lll_last_error.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU (other streams,
+ * other threads, other contexts on the same device) race and corrupt each
+ * other's results; serialise them.  Nothing in the array needs clearing
+ * between calls.  Asynchronous on the context's stream. */
+int lll_simulate_noalloc(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths,
+                         uint64_t seed, double *d_sums);
+
 /* lll_build_nig_quadrature -- Q-point Gauss rule of the weight x^2 nu(x) on
  * [-xmax, xmax], nu the NIG Levy density (Barndorff-Nielsen 1997; the paper
  * gives only kappa, Section 4).  Host computation in FP64.

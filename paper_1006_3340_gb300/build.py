@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblll.so")
 
-SOURCES = ["lll_paths.cu", "lll_tables.cu", "lll_capi.cpp", "lll_quadrature.cpp"]
+SOURCES = ["lll_paths.cu", "lll_tables.cu", "lll_capi.cpp", "lll_quadrature.cpp", "lll_noalloc.cu"]
 HEADERS = ["lll_internal.h", "lll_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

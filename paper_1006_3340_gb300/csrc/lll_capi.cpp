@@ -103,6 +103,67 @@ int default_chunk_rows(int n, int QP)
 
 }  // namespace
 
+namespace lll {
+
+int record_error(lll_ctx *ctx, int code, const char *msg) { return fail(ctx, code, msg); }
+
+// Same launch shape and arguments as lll_simulate, with no allocation: the
+// per-block scratch sizes are returned for the caller to place.
+int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, uint64_t seed,
+                LaunchPlan *plan)
+{
+    if (!ctx) return fail(nullptr, LLL_EINVAL, "ctx is NULL");
+    if (!plan) return fail(ctx, LLL_EINVAL, "plan is NULL");
+    if (scheme == LLL_MLP) return fail(ctx, LLL_ESTATE, "the MLP drift needs a trained network");
+    if (scheme != LLL_FULL && scheme != LLL_PICARD && scheme != LLL_FROZEN)
+        return fail(ctx, LLL_EINVAL, "unknown scheme");
+    if (ctx->ns == 0) return fail(ctx, LLL_ESTATE, "lll_set_strikes must come before simulating");
+    if (paths == 0) return fail(ctx, LLL_EINVAL, "paths must be > 0");
+    if (first_path + paths < first_path) return fail(ctx, LLL_EINVAL, "path range overflows");
+    const int QPk = (scheme == LLL_FROZEN) ? 0 : ctx->QP;
+    if (!path_kernel_supported(scheme, QPk)) return fail(ctx, LLL_EUNSUPPORTED, "no kernel for this Q");
+    const int T = ctx->threads, CH = ctx->chunk_rows;
+    const size_t smem = path_kernel_smem(QPk, ctx->n, ctx->ns, T, CH);
+    if (smem > 227 * 1024) return fail(ctx, LLL_EUNSUPPORTED, "shared memory need exceeds 227 KB");
+    cudaError_t e = (cudaError_t)path_kernel_prepare(scheme, QPk, smem);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+    int occ = 0;
+    e = (cudaError_t)path_kernel_occupancy(scheme, QPk, T, smem, &occ);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
+    if (occ < 1) return fail(ctx, LLL_EUNSUPPORTED, "launch shape does not fit on an SM");
+    const int bps = ctx->blocks_per_sm > 0 ? std::min(ctx->blocks_per_sm, occ) : occ;
+    const uint64_t tiles = (paths + T - 1) / T;
+    const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)bps * ctx->sm_count);
+    const int nst = (scheme == LLL_PICARD) ? 2 : 1;
+    PathArgs a{};
+    a.tab = ctx->d_tab; a.row = ctx->d_row; a.Z0 = ctx->d_Z0; a.c0 = ctx->d_c0;
+    a.strikes = ctx->d_strikes; a.partials = nullptr; a.state = nullptr;
+    a.snap = nullptr; a.n_snap = 0; a.snap_stride = 1; a.snap_pitch = 0;
+    a.first_path = first_path; a.paths = paths;
+    a.n = ctx->n; a.s = ctx->s; a.S = ctx->S; a.ns = ctx->ns; a.chunk_rows = CH;
+    a.key0 = (uint32_t)seed; a.key1 = (uint32_t)(seed >> 32); a.inst = 0;
+    a.driver = ctx->driver;
+    a.h = (float)ctx->h; a.sqrt_h = (float)std::sqrt(ctx->h); a.delta = (float)ctx->delta;
+    a.dBN = (float)(ctx->delta * ctx->BN);
+    if (ctx->driver == LLL_DRIVER_NIG) {
+        const double m = ctx->nig.delta * ctx->h / ctx->gam;
+        const double l = (ctx->nig.delta * ctx->h) * (ctx->nig.delta * ctx->h);
+        a.ig_m = (float)m; a.ig_m2 = (float)(m * m); a.ig_hl = (float)(m / (2.0 * l));
+        a.ig_fl = (float)(4.0 * m * l); a.ig_md = m; a.ig_ld = l;
+        a.nig_beta = (float)ctx->nig.beta; a.nig_muh = (float)(ctx->mu * ctx->h);
+    }
+    plan->args = a;
+    plan->scheme = scheme; plan->qp = QPk; plan->threads = T; plan->grid = grid; plan->smem = smem;
+    plan->state_floats_per_block = (size_t)nst * ctx->n * T;
+    plan->partial_doubles_per_block = (size_t)ctx->n * ctx->ns * 2;
+    plan->n_out = ctx->n * ctx->ns * 2;
+    plan->stream = ctx->stream;
+    plan->device = ctx->device;
+    return LLL_OK;
+}
+
+}  // namespace lll
+
 extern "C" {
 
 const char *lll_last_error(const lll_ctx *ctx) { return ctx ? ctx->err.c_str() : g_err.c_str(); }

@@ -37,6 +37,18 @@ struct PathArgs {
     double ig_md, ig_ld;             // m and l in FP64 for the acceptance re-check
 };
 
+// The launch lll_simulate would make for one simulation, worked out without
+// allocating anything; state and partials are left for the caller to place.
+struct LaunchPlan {
+    PathArgs args;
+    int scheme, qp, threads, grid;
+    size_t smem;
+    size_t state_floats_per_block, partial_doubles_per_block;
+    int n_out; // doubles written by the final reduction: n * n_strikes * 2
+    cudaStream_t stream;
+    int device;
+};
+
 // Launchers implemented in lll_paths.cu.  Return a cudaError_t value.
 int launch_path_kernel(int scheme, int QP, int grid, int threads, size_t smem, cudaStream_t st,
                        const PathArgs &a);
@@ -53,4 +65,12 @@ int launch_frozen_drift(const double *lam, const double *x, const double *W, con
                         cudaStream_t st);
 int launch_finalize(const double *partials, int grid, int n_out, double *sums, cudaStream_t st);
 
+}  // namespace lll
+
+struct lll_ctx;
+namespace lll {
+// Implemented in lll_capi.cpp.
+int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, uint64_t seed,
+                LaunchPlan *plan);
+int record_error(lll_ctx *ctx, int code, const char *msg);
 }  // namespace lll

@@ -58,6 +58,7 @@ def load():
         "lll_set_strikes": (I, [V, I, _dp]),
         "lll_set_snapshots": (I, [V, U64, U64]),
         "lll_simulate": (I, [V, I, U64, U64, U64]),
+        "lll_simulate_noalloc": (I, [V, I, U64, U64, U64, V]),
         "lll_get_sums": (I, [V, _dp, _dp, ctypes.POINTER(U64)]),
         "lll_price_caplets": (I, [V, _dp, _dp]),
         "lll_get_paths": (I, [V, U64, U64, _fp]),
@@ -131,6 +132,12 @@ def lll_set_snapshots(ctx, count, stride=1):
 
 def lll_simulate(ctx, scheme, first_path, paths, seed):
     _check(load().lll_simulate(ctx, int(scheme), int(first_path), int(paths), int(seed)), ctx)
+
+
+def lll_simulate_noalloc(ctx, scheme, first_path, paths, seed, d_sums: int):
+    """``d_sums``: device address of n * n_strikes * 2 doubles owned by the caller."""
+    _check(load().lll_simulate_noalloc(ctx, int(scheme), int(first_path), int(paths), int(seed),
+                                       ctypes.c_void_p(d_sums)), ctx)
 
 
 def lll_get_sums(ctx, n, ns):
