@@ -125,9 +125,12 @@ int lll_get_paths(lll_ctx *ctx, uint64_t first, uint64_t count, float *out);
 
 /* lll_set_launch -- override the launch shape of the path kernels:
  * threads per block (32..256, multiple of 32), resident blocks per SM
- * (0 = occupancy maximum), table rows staged per pipeline chunk (>= 1).
- * 0 for any argument keeps the library default. */
-int lll_set_launch(lll_ctx *ctx, int threads_per_block, int blocks_per_sm, int chunk_rows);
+ * (0 = occupancy maximum), table rows staged per pipeline chunk (>= 1),
+ * paths carried per thread (1 or 2; 2 is compiled for Q <= 64 only and
+ * shares each staged table load between two paths).  0 for any argument
+ * selects the library default. */
+int lll_set_launch(lll_ctx *ctx, int threads_per_block, int blocks_per_sm, int chunk_rows,
+                   int paths_per_thread);
 
 /* lll_kernel_ms -- device time of the last simulation's path kernel and of the
  * whole lll_simulate call, from CUDA events on the context's stream.
@@ -162,6 +165,57 @@ int lll_simulate_noalloc(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t
  * gives only kappa, Section 4).  Host computation in FP64.
  *   nodes, weights: [Q] outputs, Q in [1, 128]. */
 int lll_build_nig_quadrature(lll_nig nig, double xmax, int Q, double *nodes, double *weights);
+
+/* ---- Learned compensator (the MLP drift of LLL_MLP) -----------------------
+ * A SiLU multilayer perceptron stands in for the jump integral of
+ * Eq. (LIBOR-drift-PT) in the full scheme.  Input row (in_dim = N + 3):
+ *   (t / T_N, i / n, lambda(t, T_i) * s_lam, u_0 .. u_{N-1}),
+ *   u_m = (log L_m(t) - log L_m(0)) * s_u,
+ * output f with A_i = C_i + s_y f, where C_i is the compensator with all later
+ * weights zero (exact, from the FP64 tables).  BF16 weights and activations,
+ * FP32 accumulation (tensor cores), FP32 master weights, Adam.  Parameters
+ * are one flat FP32 vector: for each hidden layer W (hidden x in) and b,
+ * then the output w (hidden) and b (1); lll_mlp_layout gives the offsets. */
+typedef struct {
+    int hidden;           /* width of every hidden layer: 128 or 256 */
+    int layers;           /* hidden layers: 1..4 */
+    uint64_t train_paths; /* full-scheme (quadrature) paths simulated to make the data */
+    int records_per_path; /* Euler steps recorded per path (1..8), one pair per live rate each */
+    int epochs;           /* passes over the pairs */
+    int batch;            /* rows per Adam step (>= 32) */
+    double lr, lr_final;  /* Adam step size, decayed geometrically to lr_final (<= 0: constant) */
+    uint64_t seed;
+} lll_mlp_cfg;
+
+/* lll_mlp_init -- a fresh network (He-uniform weights from `seed`, zero
+ * biases) with the context's feature scales; s_y = 1 until trained. */
+int lll_mlp_init(lll_ctx *ctx, int hidden, int layers, uint64_t seed);
+
+/* lll_mlp_train -- generate training pairs with the quadrature full scheme on
+ * the GPU (paths keyed by cfg->seed, not by pricing seeds), set s_y to the RMS
+ * target, and train with Adam on the GPU.  *final_loss = MSE of the last batch
+ * in units of s_y^2.  Synchronises the stream. */
+int lll_mlp_train(lll_ctx *ctx, const lll_mlp_cfg *cfg, double *final_loss);
+
+/* lll_mlp_layout -- parameter count, input width, padded input width and the
+ * flat offsets (W_0, b_0, ..., W_{L-1}, b_{L-1}, w_out, b_out: 2L+2 values). */
+int lll_mlp_layout(lll_ctx *ctx, size_t *n_params, int *in_dim, int *in_pad, size_t *offsets);
+
+/* lll_mlp_params -- direction 0: copy the FP32 parameters and the five scales
+ * (s_t, s_i, s_lam, s_u, s_y) out; 1: copy them in (either pointer may be
+ * NULL).  count must equal the parameter count. */
+int lll_mlp_params(lll_ctx *ctx, int direction, float *params, size_t count, float *scales);
+
+/* lll_mlp_eval -- run the network on host feature rows x[rows][in_dim]:
+ * out[rows] (may be NULL).  With targets y[rows]: *loss = mean (f - y)^2, and
+ * with grads != NULL its gradient w.r.t. every parameter (flat layout). */
+int lll_mlp_eval(lll_ctx *ctx, const float *x, const float *y, int rows, float *out, float *grads,
+                 double *loss);
+
+/* lll_mlp_save / lll_mlp_load -- flat binary file: magic, (hidden, layers,
+ * in_dim, N), the five scales, parameter count, FP32 parameters. */
+int lll_mlp_save(lll_ctx *ctx, const char *path);
+int lll_mlp_load(lll_ctx *ctx, const char *path);
 
 /* lll_last_error -- message of the last failing call on ctx (ctx may be NULL:
  * the last failure of lll_init or lll_build_nig_quadrature in this thread). */

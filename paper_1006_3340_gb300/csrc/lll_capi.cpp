@@ -9,40 +9,16 @@
 #include <cuda_runtime.h>
 
 #include "../../include/lll.h"
+#include "lll_ctx.h"
 #include "lll_internal.h"
 
 namespace lll {
 int build_nig_rule(double alpha, double beta, double dbar, double a, int Q, double *nodes,
                    double *weights);
+int simulate_mlp(lll_ctx *ctx, uint64_t first_path, uint64_t paths, uint64_t seed);
 }
 
 using namespace lll;
-
-struct lll_ctx {
-    int N = 0, n = 0, s = 0, S = 0, Q = 0, QP = 0, driver = 0;
-    double delta = 0, h = 0, c = 0, mu = 0, gam = 0, BN = 0;
-    lll_nig nig{};
-    cudaStream_t stream = nullptr;
-    int device = 0, sm_count = 0;
-    std::vector<double> L0;
-    // device
-    double *d_lam = nullptr, *d_x = nullptr, *d_W = nullptr, *d_w0 = nullptr, *d_b0 = nullptr;
-    float4 *d_tab = nullptr, *d_row = nullptr;
-    float *d_Z0 = nullptr, *d_c0 = nullptr, *d_strikes = nullptr;
-    double *d_partials = nullptr, *d_sums = nullptr;
-    size_t partials_cap = 0, sums_cap = 0;
-    float *d_state = nullptr;
-    size_t state_cap = 0;
-    float *d_snap = nullptr;
-    uint64_t n_snap = 0, snap_stride = 1;
-    int ns = 0;
-    bool simulated = false;
-    uint64_t last_paths = 0;
-    uint64_t last_snap_paths = 0;
-    int threads = 128, blocks_per_sm = 0, chunk_rows = 0;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    std::string err;
-};
 
 namespace {
 
@@ -88,7 +64,9 @@ void free_all(lll_ctx *c)
     cudaFree(c->d_lam); cudaFree(c->d_x); cudaFree(c->d_W); cudaFree(c->d_w0); cudaFree(c->d_b0);
     cudaFree(c->d_tab); cudaFree(c->d_row); cudaFree(c->d_Z0); cudaFree(c->d_c0);
     cudaFree(c->d_strikes); cudaFree(c->d_partials); cudaFree(c->d_sums); cudaFree(c->d_state);
-    cudaFree(c->d_snap);
+    cudaFree(c->d_snap); cudaFree(c->d_C);
+    mlp_free(c->mlp);
+    c->mlp = nullptr;
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
 }
@@ -114,25 +92,27 @@ int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, u
 {
     if (!ctx) return fail(nullptr, LLL_EINVAL, "ctx is NULL");
     if (!plan) return fail(ctx, LLL_EINVAL, "plan is NULL");
-    if (scheme == LLL_MLP) return fail(ctx, LLL_ESTATE, "the MLP drift needs a trained network");
+    if (scheme == LLL_MLP) return fail(ctx, LLL_EUNSUPPORTED, "LLL_MLP runs through lll_simulate only");
     if (scheme != LLL_FULL && scheme != LLL_PICARD && scheme != LLL_FROZEN)
         return fail(ctx, LLL_EINVAL, "unknown scheme");
     if (ctx->ns == 0) return fail(ctx, LLL_ESTATE, "lll_set_strikes must come before simulating");
     if (paths == 0) return fail(ctx, LLL_EINVAL, "paths must be > 0");
     if (first_path + paths < first_path) return fail(ctx, LLL_EINVAL, "path range overflows");
     const int QPk = (scheme == LLL_FROZEN) ? 0 : ctx->QP;
-    if (!path_kernel_supported(scheme, QPk)) return fail(ctx, LLL_EUNSUPPORTED, "no kernel for this Q");
+    const int R = ctx->ppt > 0 ? ctx->ppt : 1;
+    if (!path_kernel_supported(scheme, QPk, R))
+        return fail(ctx, LLL_EUNSUPPORTED, "no kernel for this Q and paths per thread");
     const int T = ctx->threads, CH = ctx->chunk_rows;
     const size_t smem = path_kernel_smem(QPk, ctx->n, ctx->ns, T, CH);
     if (smem > 227 * 1024) return fail(ctx, LLL_EUNSUPPORTED, "shared memory need exceeds 227 KB");
-    cudaError_t e = (cudaError_t)path_kernel_prepare(scheme, QPk, smem);
+    cudaError_t e = (cudaError_t)path_kernel_prepare(scheme, QPk, R, smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
     int occ = 0;
-    e = (cudaError_t)path_kernel_occupancy(scheme, QPk, T, smem, &occ);
+    e = (cudaError_t)path_kernel_occupancy(scheme, QPk, R, T, smem, &occ);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
     if (occ < 1) return fail(ctx, LLL_EUNSUPPORTED, "launch shape does not fit on an SM");
     const int bps = ctx->blocks_per_sm > 0 ? std::min(ctx->blocks_per_sm, occ) : occ;
-    const uint64_t tiles = (paths + T - 1) / T;
+    const uint64_t tiles = (paths + (uint64_t)T * R - 1) / ((uint64_t)T * R);
     const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)bps * ctx->sm_count);
     const int nst = (scheme == LLL_PICARD) ? 2 : 1;
     PathArgs a{};
@@ -153,8 +133,9 @@ int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, u
         a.nig_beta = (float)ctx->nig.beta; a.nig_muh = (float)(ctx->mu * ctx->h);
     }
     plan->args = a;
-    plan->scheme = scheme; plan->qp = QPk; plan->threads = T; plan->grid = grid; plan->smem = smem;
-    plan->state_floats_per_block = (size_t)nst * ctx->n * T;
+    plan->scheme = scheme; plan->qp = QPk; plan->ppt = R; plan->threads = T; plan->grid = grid;
+    plan->smem = smem;
+    plan->state_floats_per_block = (size_t)R * nst * ctx->n * T;
     plan->partial_doubles_per_block = (size_t)ctx->n * ctx->ns * 2;
     plan->n_out = ctx->n * ctx->ns * 2;
     plan->stream = ctx->stream;
@@ -229,6 +210,7 @@ int lll_init(lll_ctx **out, int N, double tenor_delta, const double *L0, int ste
     c->nig = nig; c->mu = mu; c->gam = gam;
     c->stream = (cudaStream_t)cuda_stream;
     c->L0.assign(L0, L0 + N);
+    c->lam.assign(lambda, lambda + (size_t)S * n);
     double BN = 1.0;
     for (int m = 0; m < N; ++m) BN /= 1.0 + tenor_delta * L0[m]; // Eq. (i-val) inverted
     c->BN = BN;
@@ -258,7 +240,8 @@ int lll_init(lll_ctx **out, int N, double tenor_delta, const double *L0, int ste
               dalloc(&c->d_W, std::max(Q, 1)) == cudaSuccess && dalloc(&c->d_w0, n) == cudaSuccess &&
               dalloc(&c->d_b0, rows) == cudaSuccess &&
               dalloc(&c->d_tab, rows * std::max(QP / 2, 1)) == cudaSuccess &&
-              dalloc(&c->d_row, rows) == cudaSuccess && dalloc(&c->d_Z0, n) == cudaSuccess &&
+              dalloc(&c->d_row, rows) == cudaSuccess && dalloc(&c->d_C, rows) == cudaSuccess &&
+              dalloc(&c->d_Z0, n) == cudaSuccess &&
               dalloc(&c->d_c0, n) == cudaSuccess;
     if (!ok) { fail(c, LLL_ENOMEM, "cudaMalloc of model tables failed"); return bail(LLL_ENOMEM); }
     for (auto &ev : c->ev)
@@ -278,7 +261,7 @@ int lll_init(lll_ctx **out, int N, double tenor_delta, const double *L0, int ste
     INIT_TRY(cudaMemcpyAsync(c->d_Z0, Z0.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
     INIT_TRY(cudaMemcpyAsync(c->d_c0, c0.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
     INIT_TRY(cudaMemsetAsync(c->d_row, 0, sizeof(float4) * rows, st));
-    INIT_TRY((cudaError_t)launch_tables(c->d_lam, c->d_x, c->d_W, n, S, Q, QP, c->d_tab, c->d_row, st));
+    INIT_TRY((cudaError_t)launch_tables(c->d_lam, c->d_x, c->d_W, n, S, Q, QP, c->d_tab, c->d_row, c->d_C, st));
     INIT_TRY((cudaError_t)launch_frozen_drift(c->d_lam, c->d_x, c->d_W, c->d_w0, n, S, Q, c->c, c->h,
                                               c->d_b0, c->d_row, st));
     // The host vectors above go out of scope: wait for the copies.
@@ -328,13 +311,17 @@ int lll_set_snapshots(lll_ctx *ctx, uint64_t count, uint64_t stride)
     return LLL_OK;
 }
 
-int lll_set_launch(lll_ctx *ctx, int threads_per_block, int blocks_per_sm, int chunk_rows)
+int lll_set_launch(lll_ctx *ctx, int threads_per_block, int blocks_per_sm, int chunk_rows,
+                   int paths_per_thread)
 {
     if (!ctx) return fail(nullptr, LLL_EINVAL, "ctx is NULL");
     if (threads_per_block != 0 &&
         (threads_per_block < 32 || threads_per_block > kMaxThreads || threads_per_block % 32))
         return fail(ctx, LLL_EINVAL, "threads_per_block must be a multiple of 32 in [32, 256]");
     if (blocks_per_sm < 0 || chunk_rows < 0) return fail(ctx, LLL_EINVAL, "negative launch value");
+    if (paths_per_thread < 0 || paths_per_thread > 2)
+        return fail(ctx, LLL_EINVAL, "paths_per_thread must be 0 (automatic), 1 or 2");
+    ctx->ppt = paths_per_thread;
     if (threads_per_block) ctx->threads = threads_per_block;
     ctx->blocks_per_sm = blocks_per_sm;
     ctx->chunk_rows = chunk_rows ? std::min(chunk_rows, ctx->n) : default_chunk_rows(ctx->n, ctx->QP);
@@ -343,29 +330,15 @@ int lll_set_launch(lll_ctx *ctx, int threads_per_block, int blocks_per_sm, int c
 
 int lll_simulate(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, uint64_t seed)
 {
-    if (!ctx) return fail(nullptr, LLL_EINVAL, "ctx is NULL");
-    if (scheme == LLL_MLP) return fail(ctx, LLL_ESTATE, "the MLP drift needs a trained network");
-    if (scheme != LLL_FULL && scheme != LLL_PICARD && scheme != LLL_FROZEN)
-        return fail(ctx, LLL_EINVAL, "unknown scheme");
-    if (ctx->ns == 0) return fail(ctx, LLL_ESTATE, "lll_set_strikes must come before lll_simulate");
-    if (paths == 0) return fail(ctx, LLL_EINVAL, "paths must be > 0");
-    if (first_path + paths < first_path) return fail(ctx, LLL_EINVAL, "path range overflows");
-    const int QPk = (scheme == LLL_FROZEN) ? 0 : ctx->QP;
-    if (!path_kernel_supported(scheme, QPk)) return fail(ctx, LLL_EUNSUPPORTED, "no kernel for this Q");
-    const int T = ctx->threads, CH = ctx->chunk_rows;
-    const size_t smem = path_kernel_smem(QPk, ctx->n, ctx->ns, T, CH);
-    if (smem > 227 * 1024) return fail(ctx, LLL_EUNSUPPORTED, "shared memory need exceeds 227 KB");
-    cudaError_t e = (cudaError_t)path_kernel_prepare(scheme, QPk, smem);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
-    int occ = 0;
-    e = (cudaError_t)path_kernel_occupancy(scheme, QPk, T, smem, &occ);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
-    if (occ < 1) return fail(ctx, LLL_EUNSUPPORTED, "launch shape does not fit on an SM");
-    const int bps = ctx->blocks_per_sm > 0 ? std::min(ctx->blocks_per_sm, occ) : occ;
-    const uint64_t tiles = (paths + T - 1) / T;
-    const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)bps * ctx->sm_count);
-    const int nst = (scheme == LLL_PICARD) ? 2 : 1;
-    const size_t state_need = (size_t)grid * nst * ctx->n * T;
+    if (ctx && scheme == LLL_MLP) {
+        if (ctx->ns == 0) return fail(ctx, LLL_ESTATE, "lll_set_strikes must come before lll_simulate");
+        return simulate_mlp(ctx, first_path, paths, seed);
+    }
+    LaunchPlan plan;
+    int rc = plan_launch(ctx, scheme, first_path, paths, seed, &plan);
+    if (rc != LLL_OK) return rc;
+    const int grid = plan.grid;
+    const size_t state_need = plan.state_floats_per_block * grid;
     if (state_need > ctx->state_cap) {
         cudaFree(ctx->d_state);
         ctx->d_state = nullptr;
@@ -373,7 +346,7 @@ int lll_simulate(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, 
         if (dalloc(&ctx->d_state, state_need) != cudaSuccess) return fail(ctx, LLL_ENOMEM, "state scratch");
         ctx->state_cap = state_need;
     }
-    const size_t nout = (size_t)ctx->n * ctx->ns * 2;
+    const size_t nout = (size_t)plan.n_out;
     if ((size_t)grid * nout > ctx->partials_cap) {
         cudaFree(ctx->d_partials);
         ctx->d_partials = nullptr;
@@ -389,26 +362,16 @@ int lll_simulate(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, 
         if (dalloc(&ctx->d_sums, nout) != cudaSuccess) return fail(ctx, LLL_ENOMEM, "sums");
         ctx->sums_cap = nout;
     }
-    PathArgs a{};
-    a.tab = ctx->d_tab; a.row = ctx->d_row; a.Z0 = ctx->d_Z0; a.c0 = ctx->d_c0;
-    a.strikes = ctx->d_strikes; a.partials = ctx->d_partials; a.state = ctx->d_state;
+    PathArgs a = plan.args;
+    a.partials = ctx->d_partials;
+    a.state = ctx->d_state;
     a.snap = ctx->d_snap; a.snap_stride = ctx->snap_stride; a.snap_pitch = ctx->n_snap;
     a.n_snap = ctx->d_snap ? std::min<uint64_t>(ctx->n_snap, (paths + ctx->snap_stride - 1) / ctx->snap_stride) : 0;
-    a.first_path = first_path; a.paths = paths;
-    a.n = ctx->n; a.s = ctx->s; a.S = ctx->S; a.ns = ctx->ns; a.chunk_rows = CH;
-    a.key0 = (uint32_t)seed; a.key1 = (uint32_t)(seed >> 32); a.inst = 0;
-    a.driver = ctx->driver;
-    a.h = (float)ctx->h; a.sqrt_h = (float)std::sqrt(ctx->h); a.delta = (float)ctx->delta;
-    a.dBN = (float)(ctx->delta * ctx->BN);
-    if (ctx->driver == LLL_DRIVER_NIG) {
-        const double m = ctx->nig.delta * ctx->h / ctx->gam;
-        const double l = (ctx->nig.delta * ctx->h) * (ctx->nig.delta * ctx->h);
-        a.ig_m = (float)m; a.ig_m2 = (float)(m * m); a.ig_hl = (float)(m / (2.0 * l));
-        a.ig_fl = (float)(4.0 * m * l); a.ig_md = m; a.ig_ld = l;
-        a.nig_beta = (float)ctx->nig.beta; a.nig_muh = (float)(ctx->mu * ctx->h);
-    }
+    const int QPk = plan.qp, T = plan.threads;
+    const size_t smem = plan.smem;
+    cudaError_t e;
     CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
-    e = (cudaError_t)launch_path_kernel(scheme, QPk, grid, T, smem, ctx->stream, a);
+    e = (cudaError_t)launch_path_kernel(scheme, QPk, plan.ppt, grid, T, smem, ctx->stream, a);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "path kernel launch");
     CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
     e = (cudaError_t)launch_finalize(ctx->d_partials, grid, (int)nout, ctx->d_sums, ctx->stream);

@@ -1,0 +1,44 @@
+// lll_ctx.h -- the model context behind the opaque lll_ctx handle (private).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lll.h"
+
+namespace lll {
+struct MlpState;
+void mlp_free(MlpState *m);
+}  // namespace lll
+
+struct lll_ctx {
+    int N = 0, n = 0, s = 0, S = 0, Q = 0, QP = 0, driver = 0;
+    double delta = 0, h = 0, c = 0, mu = 0, gam = 0, BN = 0;
+    lll_nig nig{};
+    cudaStream_t stream = nullptr;
+    int device = 0, sm_count = 0;
+    std::vector<double> L0;
+    // device
+    double *d_lam = nullptr, *d_x = nullptr, *d_W = nullptr, *d_w0 = nullptr, *d_b0 = nullptr;
+    float4 *d_tab = nullptr, *d_row = nullptr;
+    float *d_C = nullptr; // [S][n]: C_l(t_k), the compensator at zero weights (FP64-built)
+    float *d_Z0 = nullptr, *d_c0 = nullptr, *d_strikes = nullptr;
+    double *d_partials = nullptr, *d_sums = nullptr;
+    size_t partials_cap = 0, sums_cap = 0;
+    float *d_state = nullptr;
+    size_t state_cap = 0;
+    float *d_snap = nullptr;
+    uint64_t n_snap = 0, snap_stride = 1;
+    int ns = 0;
+    bool simulated = false;
+    uint64_t last_paths = 0;
+    uint64_t last_snap_paths = 0;
+    int threads = 128, blocks_per_sm = 0, chunk_rows = 0, ppt = 0; // ppt 0: automatic
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    std::vector<double> lam; // host copy of lambda [S][n]
+    lll::MlpState *mlp = nullptr;
+    std::string err;
+};

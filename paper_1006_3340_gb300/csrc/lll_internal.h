@@ -41,7 +41,7 @@ struct PathArgs {
 // allocating anything; state and partials are left for the caller to place.
 struct LaunchPlan {
     PathArgs args;
-    int scheme, qp, threads, grid;
+    int scheme, qp, ppt, threads, grid;
     size_t smem;
     size_t state_floats_per_block, partial_doubles_per_block;
     int n_out; // doubles written by the final reduction: n * n_strikes * 2
@@ -50,16 +50,17 @@ struct LaunchPlan {
 };
 
 // Launchers implemented in lll_paths.cu.  Return a cudaError_t value.
-int launch_path_kernel(int scheme, int QP, int grid, int threads, size_t smem, cudaStream_t st,
+// R = paths carried per thread (1, or 2 where compiled: padded Q <= 64).
+int launch_path_kernel(int scheme, int QP, int R, int grid, int threads, size_t smem, cudaStream_t st,
                        const PathArgs &a);
-int path_kernel_occupancy(int scheme, int QP, int threads, size_t smem, int *blocks_per_sm);
-int path_kernel_prepare(int scheme, int QP, size_t smem);
-bool path_kernel_supported(int scheme, int QP);
+int path_kernel_occupancy(int scheme, int QP, int R, int threads, size_t smem, int *blocks_per_sm);
+int path_kernel_prepare(int scheme, int QP, int R, size_t smem);
+bool path_kernel_supported(int scheme, int QP, int R);
 size_t path_kernel_smem(int QP, int n, int ns, int threads, int chunk_rows);
 
 // Launchers implemented in lll_tables.cu.
 int launch_tables(const double *lam, const double *x, const double *W, int n, int S, int Q, int QP,
-                  float4 *tab, float4 *row, cudaStream_t st);
+                  float4 *tab, float4 *row, float *Ctab, cudaStream_t st);
 int launch_frozen_drift(const double *lam, const double *x, const double *W, const double *w0,
                         int n, int S, int Q, double c, double h, double *b0, float4 *row,
                         cudaStream_t st);

@@ -1,0 +1,57 @@
+// lll_mlp.h -- launch helpers of the MLP kernels (lll_mlp.cu, lll_mlp_path.cu).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "lll_internal.h"
+
+namespace lll {
+
+// Split-K aware BF16 GEMM (see lll_mlp.cu for the operand conventions).
+int mlp_gemm(int ta, int tb, int epi, const void *A, int lda, const void *B, int ldb, int M, int N,
+             int K, int splits, float *C, const float *bias, const float *Zin, float *Zout, void *Hout,
+             cudaStream_t st);
+int mlp_splits_used(int K, int splits);
+int mlp_out_loss(const void *H, int Hdim, const void *w, const float *b, const float *y, int rows,
+                 float *out, float *dout, double *loss_part, cudaStream_t st);
+int mlp_out_backward(const float *dout, const void *w, const float *Z, int rows, int Hdim, float *dZ,
+                     void *dZh, cudaStream_t st);
+int mlp_out_weight_grad(const float *dout, const void *H, int rows, int Hdim, float *gw, float *gb,
+                        cudaStream_t st);
+int mlp_column_sums(const float *X, int rows, int cols, float *out, cudaStream_t st);
+int mlp_reduce_splits(const float *part, int splits, size_t count, float *out, cudaStream_t st);
+int mlp_adam(float *p, const float *g, float *m, float *v, void *ph, size_t count, float lr, float b1,
+             float b2, float eps, int t, cudaStream_t st);
+int mlp_to_bf16(const float *x, size_t count, void *y, cudaStream_t st);
+
+// Feature scaling of the network input row (see lll_mlp.cu).
+struct MlpScales {
+    float t_scale;      // 1 / T_N
+    float i_scale;      // 1 / n
+    float lam_scale;    // 1 / lambda_ref
+    float u_scale;      // multiplier of log L_m(t) - log L_m(0)
+    float y_scale;      // target unit: A_i - C_i = y_scale * f(x)
+};
+
+// Network arguments of the fused LLL_MLP path kernel.
+struct MlpArgs {
+    const __nv_bfloat16 *wh; // BF16 copy of the flat parameters
+    const float *wp;         // FP32 flat parameters (biases are read from here)
+    size_t offW[4], offb[4], off_wout, off_bout;
+    MlpScales sc;
+    const float *Ctab;       // [S][n] compensator at zero weights
+};
+
+// lll_mlp_path.cu
+int mlp_path_threads();
+size_t mlp_path_smem(int layers, int in_pad, int n, int ns);
+bool mlp_path_supported(int hidden, int layers, int in_pad);
+int mlp_path_occupancy(int layers, int in_pad, size_t smem, int *blocks_per_sm);
+int launch_mlp_path(int layers, int in_pad, int grid, size_t smem, cudaStream_t st, const PathArgs &a,
+                    const MlpArgs &g);
+
+}  // namespace lll

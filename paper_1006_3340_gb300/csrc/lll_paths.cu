@@ -122,7 +122,7 @@ __device__ __forceinline__ void issue_chunk(const PathArgs &a, const Smem &sm, i
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) cp_async16(sm.row + b * CH + e, a.row + r0 + e);
 }
 
-template <int SCHEME, int QP>
+template <int SCHEME, int QP, int R>
 __global__ void __launch_bounds__(kMaxThreads) path_kernel(const PathArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -135,18 +135,27 @@ __global__ void __launch_bounds__(kMaxThreads) path_kernel(const PathArgs a)
     for (int e = tid; e < n; e += T) sm.c0[e] = a.c0[e];
     for (int e = tid; e < 4 * n * ns; e += T) sm.bsum[e] = 0.0;
 
-    float *st = a.state + (size_t)blockIdx.x * NST * n * T + tid;
-    const uint64_t ntiles = (a.paths + T - 1) / T;
+    // This block's state slot: [R][NST][n][T]; thread tid owns column tid.
+    float *st = a.state + (size_t)blockIdx.x * R * NST * n * T + tid;
+    const size_t rs = (size_t)NST * n * T; // stride between the R paths of a thread
+    const uint64_t TP = (uint64_t)T * R;   // paths per tile
+    const uint64_t ntiles = (a.paths + TP - 1) / TP;
     const float h = a.h, delta = a.delta;
 
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint64_t lp = tile * (uint64_t)T + tid; // path index within this simulation
-        const bool active = lp < a.paths;
-        const uint64_t p = a.first_path + lp;
-        uint64_t sidx = ~0ull; // snapshot slot of this path, if it is recorded
-        if (a.snap != nullptr && active && lp % a.snap_stride == 0 && lp / a.snap_stride < a.n_snap)
-            sidx = lp / a.snap_stride;
-        for (int l = 0; l < NST * n; ++l) st[(size_t)l * T] = 0.0f;
+        uint64_t lp[R], p[R], sidx[R];
+        bool active[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            lp[q] = tile * TP + (uint64_t)q * T + tid; // path index within this simulation
+            active[q] = lp[q] < a.paths;
+            p[q] = a.first_path + lp[q];
+            sidx[q] = ~0ull; // snapshot slot of this path, if it is recorded
+            if (a.snap != nullptr && active[q] && lp[q] % a.snap_stride == 0 &&
+                lp[q] / a.snap_stride < a.n_snap)
+                sidx[q] = lp[q] / a.snap_stride;
+        }
+        for (int l = 0; l < R * NST * n; ++l) st[(size_t)l * T] = 0.0f;
 
         __syncthreads(); // previous tile's readers of both buffers are done
         issue_chunk<QP>(a, sm, 0, 0, 0);
@@ -157,12 +166,18 @@ __global__ void __launch_bounds__(kMaxThreads) path_kernel(const PathArgs a)
             const int imin = k / s + 1;
             const int nch = (n - imin + CH) / CH; // ceil((n - imin + 1) / CH)
             const bool mat = (k + 1) % s == 0;     // rate imin fixes at t_{k+1} = T_imin
-            const float dH = draw_increment(a, p, (uint32_t)k);
-
-            float2 P[Q2];
+            float dH[R];
 #pragma unroll
-            for (int j = 0; j < Q2; ++j) P[j] = make_float2(1.0f, 1.0f);
-            float scont = 0.0f, num = 1.0f, Lm = 0.0f;
+            for (int q = 0; q < R; ++q) dH[q] = draw_increment(a, p[q], (uint32_t)k);
+
+            float2 P[R][Q2];
+#pragma unroll
+            for (int q = 0; q < R; ++q)
+#pragma unroll
+                for (int j = 0; j < Q2; ++j) P[q][j] = make_float2(1.0f, 1.0f);
+            float scont[R], num[R], Lm[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) { scont[q] = 0.0f; num[q] = 1.0f; Lm[q] = 0.0f; }
 
             for (int c = 0; c < nch; ++c) {
                 int nk = k, nc = c + 1;
@@ -176,61 +191,97 @@ __global__ void __launch_bounds__(kMaxThreads) path_kernel(const PathArgs a)
                 const int ibot = max(imin, itop - CH + 1);
                 const float4 *tb = sm.tab + (size_t)buf * CH * Q2;
                 const float4 *rb = sm.row + buf * CH;
+                // state of the first row; each row prefetches the next one's
+                float c0v[R], c1v[R];
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    c0v[q] = st[q * rs + (size_t)(itop - 1) * T];
+                    c1v[q] = (NST == 2) ? st[q * rs + (size_t)(n + itop - 1) * T] : 0.0f;
+                }
                 for (int i = itop; i >= ibot; --i) {
                     const int r = i - ibot;
                     const float4 rc = rb[r]; // lambda, K, D0, b0*h
-                    float *sp = st + (size_t)(i - 1) * T;
-                    float v0 = sp[0];
-                    float v1 = (NST == 2) ? sp[(size_t)n * T] : 0.0f;
-                    float bh;
+                    float v0[R], v1[R];
+#pragma unroll
+                    for (int q = 0; q < R; ++q) {
+                        v0[q] = c0v[q];
+                        v1[q] = c1v[q];
+                        if (i > ibot) {
+                            c0v[q] = st[q * rs + (size_t)(i - 2) * T];
+                            if (NST == 2) c1v[q] = st[q * rs + (size_t)(n + i - 2) * T];
+                        }
+                    }
+                    float bh[R];
                     if (SCHEME == FROZEN) {
-                        bh = rc.w;
+#pragma unroll
+                        for (int q = 0; q < R; ++q) bh[q] = rc.w;
                     } else {
-                        const float zoff = (SCHEME == FULL) ? v0 : (rc.z + v0);
-                        const float x = sm.c0[i - 1] + zoff; // log(delta L) at t_k
-                        const float w = __frcp_rn(1.0f + __expf(-x)); // delta L / (1 + delta L)
-                        float b;
+                        const float cx = sm.c0[i - 1];
+                        float w[R];
+#pragma unroll
+                        for (int q = 0; q < R; ++q) {
+                            const float zoff = (SCHEME == FULL) ? v0[q] : (rc.z + v0[q]);
+                            // delta L / (1 + delta L) with log(delta L) = cx + zoff
+                            w[q] = __frcp_rn(1.0f + __expf(-(cx + zoff)));
+                        }
                         if (QP > 0) {
                             const float4 *tr = tb + (size_t)r * Q2;
-                            float2 acc[4];
+                            float2 acc[R][4];
+                            float2 w2[R];
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.0f, 0.0f);
-                            const float2 w2 = make_float2(w, w);
+                            for (int q = 0; q < R; ++q) {
+                                w2[q] = make_float2(w[q], w[q]);
+#pragma unroll
+                                for (int u = 0; u < 4; ++u) acc[q][u] = make_float2(0.0f, 0.0f);
+                            }
 #pragma unroll
                             for (int j = 0; j < Q2; ++j) {
                                 const float4 v = tr[j];
                                 const float2 e2 = make_float2(v.x, v.y);
                                 const float2 a2 = make_float2(v.z, v.w);
-                                acc[j & 3] = __ffma2_rn(a2, P[j], acc[j & 3]);
-                                P[j] = __ffma2_rn(__fmul2_rn(w2, e2), P[j], P[j]);
+#pragma unroll
+                                for (int q = 0; q < R; ++q) {
+                                    acc[q][j & 3] = __ffma2_rn(a2, P[q][j], acc[q][j & 3]);
+                                    P[q][j] = __ffma2_rn(__fmul2_rn(w2[q], e2), P[q][j], P[q][j]);
+                                }
                             }
-                            const float Ai = rc.y + (((acc[0].x + acc[0].y) + (acc[1].x + acc[1].y)) +
-                                                     ((acc[2].x + acc[2].y) + (acc[3].x + acc[3].y)));
-                            b = -Ai;
+#pragma unroll
+                            for (int q = 0; q < R; ++q) {
+                                const float Ai =
+                                    rc.y + (((acc[q][0].x + acc[q][0].y) + (acc[q][1].x + acc[q][1].y)) +
+                                            ((acc[q][2].x + acc[q][2].y) + (acc[q][3].x + acc[q][3].y)));
+                                bh[q] = -Ai * h;
+                            }
                         } else {
-                            b = -0.5f * rc.x * rc.x - rc.x * scont;
-                            scont = fmaf(w, rc.x, scont);
+#pragma unroll
+                            for (int q = 0; q < R; ++q) {
+                                bh[q] = (-0.5f * rc.x * rc.x - rc.x * scont[q]) * h;
+                                scont[q] = fmaf(w[q], rc.x, scont[q]);
+                            }
                         }
-                        bh = b * h;
                     }
-                    float znew;
-                    if (SCHEME == PICARD) {
-                        v0 = fmaf(rc.x, dH, v0); // int lambda dH
-                        v1 += bh;                // Picard drift integral
-                        sp[0] = v0;
-                        sp[(size_t)n * T] = v1;
-                        znew = v0 + v1;
-                    } else {
-                        v0 += fmaf(rc.x, dH, bh);
-                        sp[0] = v0;
-                        znew = v0;
-                    }
-                    if (mat) {
-                        znew += a.Z0[i - 1];
-                        if (i > imin) num *= fmaf(delta, expf(znew), 1.0f);
-                        else Lm = expf(znew);
-                        if (sidx != ~0ull)
-                            a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = znew;
+#pragma unroll
+                    for (int q = 0; q < R; ++q) {
+                        float *sp = st + q * rs + (size_t)(i - 1) * T;
+                        float znew;
+                        if (SCHEME == PICARD) {
+                            const float y = fmaf(rc.x, dH[q], v0[q]); // int lambda dH
+                            const float d = v1[q] + bh[q];            // Picard drift integral
+                            sp[0] = y;
+                            sp[(size_t)n * T] = d;
+                            znew = y + d;
+                        } else {
+                            const float z = v0[q] + fmaf(rc.x, dH[q], bh[q]);
+                            sp[0] = z;
+                            znew = z;
+                        }
+                        if (mat) {
+                            znew += a.Z0[i - 1];
+                            if (i > imin) num[q] *= fmaf(delta, expf(znew), 1.0f);
+                            else Lm[q] = expf(znew);
+                            if (sidx[q] != ~0ull)
+                                a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx[q]] = znew;
+                        }
                     }
                 }
                 __syncthreads();
@@ -241,9 +292,15 @@ __global__ void __launch_bounds__(kMaxThreads) path_kernel(const PathArgs a)
                 const int m = imin;
                 for (int q = 0; q < ns; ++q) {
                     const float K = a.strikes[(size_t)(m - 1) * ns + q];
-                    const double pay = active ? (double)(a.dBN * num * fmaxf(Lm - K, 0.0f)) : 0.0;
+                    double pay = 0.0, pay2 = 0.0;
+#pragma unroll
+                    for (int u = 0; u < R; ++u) {
+                        const double v = active[u] ? (double)(a.dBN * num[u] * fmaxf(Lm[u] - K, 0.0f)) : 0.0;
+                        pay += v;
+                        pay2 += v * v;
+                    }
                     const double s1 = warp_sum(pay);
-                    const double s2 = warp_sum(pay * pay);
+                    const double s2 = warp_sum(pay2);
                     if (lane == 0) {
                         sm.red[((size_t)warp * ns + q) * 2 + 0] = s1;
                         sm.red[((size_t)warp * ns + q) * 2 + 1] = s2;
@@ -275,57 +332,70 @@ __global__ void __launch_bounds__(kMaxThreads) path_kernel(const PathArgs a)
 
 typedef void (*KernelFn)(const PathArgs);
 
+// Paths per thread: 2 shares every staged table load between two paths
+// (halving shared-memory traffic per unit); compiled where the registers of
+// two node arrays fit (padded Q <= 64).
+template <int SCHEME, int QP>
+KernelFn pick_r(int R)
+{
+    if (R == 1) return path_kernel<SCHEME, QP, 1>;
+    if constexpr (QP <= 64) {
+        if (R == 2) return path_kernel<SCHEME, QP, 2>;
+    }
+    return nullptr;
+}
+
 template <int SCHEME>
-KernelFn pick_qp(int QP)
+KernelFn pick_qp(int QP, int R)
 {
     switch (QP) {
-    case 0: return path_kernel<SCHEME, 0>;
-    case 16: return path_kernel<SCHEME, 16>;
-    case 32: return path_kernel<SCHEME, 32>;
-    case 64: return path_kernel<SCHEME, 64>;
-    case 96: return path_kernel<SCHEME, 96>;
-    case 128: return path_kernel<SCHEME, 128>;
+    case 0: return pick_r<SCHEME, 0>(R);
+    case 16: return pick_r<SCHEME, 16>(R);
+    case 32: return pick_r<SCHEME, 32>(R);
+    case 64: return pick_r<SCHEME, 64>(R);
+    case 96: return pick_r<SCHEME, 96>(R);
+    case 128: return pick_r<SCHEME, 128>(R);
     default: return nullptr;
     }
 }
 
-KernelFn pick(int scheme, int QP)
+KernelFn pick(int scheme, int QP, int R)
 {
     switch (scheme) {
-    case FULL: return pick_qp<FULL>(QP);
-    case PICARD: return pick_qp<PICARD>(QP);
-    case FROZEN: return path_kernel<FROZEN, 0>;
+    case FULL: return pick_qp<FULL>(QP, R);
+    case PICARD: return pick_qp<PICARD>(QP, R);
+    case FROZEN: return pick_r<FROZEN, 0>(R);
     default: return nullptr;
     }
 }
 
 }  // namespace
 
-bool path_kernel_supported(int scheme, int QP) { return pick(scheme, QP) != nullptr; }
+bool path_kernel_supported(int scheme, int QP, int R) { return pick(scheme, QP, R) != nullptr; }
 
 size_t path_kernel_smem(int QP, int n, int ns, int threads, int chunk_rows)
 {
     return smem_bytes(QP, n, ns, threads, chunk_rows);
 }
 
-int path_kernel_prepare(int scheme, int QP, size_t smem)
+int path_kernel_prepare(int scheme, int QP, int R, size_t smem)
 {
-    KernelFn f = pick(scheme, QP);
+    KernelFn f = pick(scheme, QP, R);
     if (!f) return (int)cudaErrorInvalidValue;
     return (int)cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-int path_kernel_occupancy(int scheme, int QP, int threads, size_t smem, int *blocks_per_sm)
+int path_kernel_occupancy(int scheme, int QP, int R, int threads, size_t smem, int *blocks_per_sm)
 {
-    KernelFn f = pick(scheme, QP);
+    KernelFn f = pick(scheme, QP, R);
     if (!f) return (int)cudaErrorInvalidValue;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, smem);
 }
 
-int launch_path_kernel(int scheme, int QP, int grid, int threads, size_t smem, cudaStream_t st,
+int launch_path_kernel(int scheme, int QP, int R, int grid, int threads, size_t smem, cudaStream_t st,
                        const PathArgs &a)
 {
-    KernelFn f = pick(scheme, QP);
+    KernelFn f = pick(scheme, QP, R);
     if (!f) return (int)cudaErrorInvalidValue;
     // The frozen kernel stages no node table; its QP argument is ignored.
     f<<<grid, threads, smem, st>>>(a);

@@ -5,6 +5,7 @@
 //   a_lj = W_j E_lj / x_j^2 (rounded to FP32), and the constant
 //   K_l = C_l - sum_j fl32(a_lj), C_l = sum_j W_j (E_lj - lambda_l x_j) / x_j^2,
 //   so that A_l = K_l + sum_j a_lj P_j reproduces C_l exactly when P = 1.
+//   C_l itself (the compensator with all later weights zero) is kept too.
 // frozen_drift_kernel: the drift b(t_k, T_l; Z(0)) of Eq. (Picard-2), i.e.
 //   Eq. (LIBOR-drift-PT) with L frozen at L(0), one block per step and one
 //   thread per node, a fixed-order block sum per rate.
@@ -19,7 +20,7 @@ namespace lll {
 namespace {
 
 __global__ void tables_kernel(const double *lam, const double *x, const double *W, int n, int S,
-                              int Q, int QP, float4 *tab, float4 *row)
+                              int Q, int QP, float4 *tab, float4 *row, float *Ctab)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= S * n) return;
@@ -44,6 +45,7 @@ __global__ void tables_kernel(const double *lam, const double *x, const double *
     r.x = (float)li;
     r.y = (float)(C - sa);
     row[idx] = r;
+    Ctab[idx] = (float)C;
 }
 
 __global__ void frozen_drift_kernel(const double *lam, const double *x, const double *W,
@@ -106,10 +108,10 @@ __global__ void finalize_kernel(const double *partials, int grid, int n_out, dou
 }  // namespace
 
 int launch_tables(const double *lam, const double *x, const double *W, int n, int S, int Q, int QP,
-                  float4 *tab, float4 *row, cudaStream_t st)
+                  float4 *tab, float4 *row, float *Ctab, cudaStream_t st)
 {
     const int total = S * n;
-    tables_kernel<<<(total + 127) / 128, 128, 0, st>>>(lam, x, W, n, S, Q, QP, tab, row);
+    tables_kernel<<<(total + 127) / 128, 128, 0, st>>>(lam, x, W, n, S, Q, QP, tab, row, Ctab);
     return (int)cudaGetLastError();
 }
 

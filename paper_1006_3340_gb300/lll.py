@@ -29,6 +29,12 @@ class LLLError(RuntimeError):
         self.code = code
 
 
+class lll_mlp_cfg(ctypes.Structure):
+    _fields_ = [("hidden", ctypes.c_int), ("layers", ctypes.c_int), ("train_paths", ctypes.c_uint64),
+                ("records_per_path", ctypes.c_int), ("epochs", ctypes.c_int), ("batch", ctypes.c_int),
+                ("lr", ctypes.c_double), ("lr_final", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
 class lll_nig(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double),
                 ("delta", ctypes.c_double), ("mu", ctypes.c_double)]
@@ -62,9 +68,17 @@ def load():
         "lll_get_sums": (I, [V, _dp, _dp, ctypes.POINTER(U64)]),
         "lll_price_caplets": (I, [V, _dp, _dp]),
         "lll_get_paths": (I, [V, U64, U64, _fp]),
-        "lll_set_launch": (I, [V, I, I, I]),
+        "lll_set_launch": (I, [V, I, I, I, I]),
         "lll_kernel_ms": (I, [V, _fp, _fp]),
         "lll_build_nig_quadrature": (I, [lll_nig, ctypes.c_double, I, _dp, _dp]),
+        "lll_mlp_init": (I, [V, I, I, U64]),
+        "lll_mlp_train": (I, [V, ctypes.POINTER(lll_mlp_cfg), _dp]),
+        "lll_mlp_layout": (I, [V, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(I), ctypes.POINTER(I),
+                               ctypes.POINTER(ctypes.c_size_t)]),
+        "lll_mlp_params": (I, [V, I, _fp, ctypes.c_size_t, _fp]),
+        "lll_mlp_eval": (I, [V, _fp, _fp, I, _fp, _fp, _dp]),
+        "lll_mlp_save": (I, [V, ctypes.c_char_p]),
+        "lll_mlp_load": (I, [V, ctypes.c_char_p]),
         "lll_last_error": (ctypes.c_char_p, [V]),
         "lll_destroy": (None, [V]),
     }
@@ -161,8 +175,9 @@ def lll_get_paths(ctx, n, first, count):
     return out
 
 
-def lll_set_launch(ctx, threads=0, blocks_per_sm=0, chunk_rows=0):
-    _check(load().lll_set_launch(ctx, int(threads), int(blocks_per_sm), int(chunk_rows)), ctx)
+def lll_set_launch(ctx, threads=0, blocks_per_sm=0, chunk_rows=0, paths_per_thread=0):
+    _check(load().lll_set_launch(ctx, int(threads), int(blocks_per_sm), int(chunk_rows),
+                                 int(paths_per_thread)), ctx)
 
 
 def lll_kernel_ms(ctx):
@@ -170,6 +185,62 @@ def lll_kernel_ms(ctx):
     b = ctypes.c_float()
     _check(load().lll_kernel_ms(ctx, ctypes.byref(a), ctypes.byref(b)), ctx)
     return a.value, b.value
+
+
+def lll_mlp_init(ctx, hidden, layers, seed=0):
+    _check(load().lll_mlp_init(ctx, int(hidden), int(layers), int(seed)), ctx)
+
+
+def lll_mlp_train(ctx, hidden=128, layers=3, train_paths=1 << 16, records_per_path=8, epochs=4,
+                  batch=8192, lr=2e-3, lr_final=2e-4, seed=7):
+    cfg = lll_mlp_cfg(int(hidden), int(layers), int(train_paths), int(records_per_path), int(epochs),
+                      int(batch), float(lr), float(lr_final), int(seed))
+    loss = ctypes.c_double()
+    _check(load().lll_mlp_train(ctx, ctypes.byref(cfg), ctypes.byref(loss)), ctx)
+    return loss.value
+
+
+def lll_mlp_layout(ctx, layers):
+    n = ctypes.c_size_t()
+    ind = ctypes.c_int()
+    inp = ctypes.c_int()
+    offs = (ctypes.c_size_t * (2 * layers + 2))()
+    _check(load().lll_mlp_layout(ctx, ctypes.byref(n), ctypes.byref(ind), ctypes.byref(inp), offs), ctx)
+    return n.value, ind.value, inp.value, list(offs)
+
+
+def lll_mlp_params(ctx, direction, params=None, count=None, scales=None):
+    """direction 0: returns (params, scales); 1: sets them."""
+    if direction == 0:
+        p = np.zeros(count, dtype=np.float32)
+        sc = np.zeros(5, dtype=np.float32)
+        _check(load().lll_mlp_params(ctx, 0, p.ctypes.data_as(_fp), p.size, sc.ctypes.data_as(_fp)), ctx)
+        return p, sc
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    sc = None if scales is None else np.ascontiguousarray(scales, dtype=np.float32)
+    _check(load().lll_mlp_params(ctx, 1, p.ctypes.data_as(_fp), p.size,
+                                 None if sc is None else sc.ctypes.data_as(_fp)), ctx)
+
+
+def lll_mlp_eval(ctx, x, y=None, n_params=None, want_grads=False):
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    rows = x.shape[0]
+    out = np.zeros(rows, dtype=np.float32)
+    yy = None if y is None else np.ascontiguousarray(y, dtype=np.float32)
+    g = np.zeros(n_params, dtype=np.float32) if want_grads else None
+    loss = ctypes.c_double()
+    _check(load().lll_mlp_eval(ctx, x.ctypes.data_as(_fp), None if yy is None else yy.ctypes.data_as(_fp),
+                               rows, out.ctypes.data_as(_fp), None if g is None else g.ctypes.data_as(_fp),
+                               ctypes.byref(loss)), ctx)
+    return out, g, loss.value
+
+
+def lll_mlp_save(ctx, path):
+    _check(load().lll_mlp_save(ctx, str(path).encode()), ctx)
+
+
+def lll_mlp_load(ctx, path):
+    _check(load().lll_mlp_load(ctx, str(path).encode()), ctx)
 
 
 def lll_last_error(ctx=None) -> str:
@@ -225,8 +296,8 @@ class LevyLibor:
     def kernel_ms(self):
         return lll_kernel_ms(self.ctx)
 
-    def set_launch(self, threads=0, blocks_per_sm=0, chunk_rows=0):
-        lll_set_launch(self.ctx, threads, blocks_per_sm, chunk_rows)
+    def set_launch(self, threads=0, blocks_per_sm=0, chunk_rows=0, paths_per_thread=0):
+        lll_set_launch(self.ctx, threads, blocks_per_sm, chunk_rows, paths_per_thread)
 
     def close(self):
         if self.ctx:

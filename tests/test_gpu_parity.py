@@ -87,7 +87,8 @@ def test_tiny_edge_shapes(lll, N, s, Q, paths, scheme):
     _compare(lll, wl, scheme, paths)
 
 
-@pytest.mark.parametrize("launch", [(32, 0, 1), (64, 1, 2), (256, 0, 3), (96, 2, 0)])
+@pytest.mark.parametrize("launch", [(32, 0, 1, 1), (64, 1, 2, 2), (256, 0, 3, 1), (96, 2, 0, 2),
+                                    (128, 0, 0, 1), (256, 0, 0, 2)])
 def test_launch_shapes_agree(lll, launch):
     wl = workloads.large_single()
     _compare(lll, wl, "picard", 300, launch=launch)
