@@ -180,7 +180,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--paths", type=int, default=0, help="paths per GPU (default 2^20)")
     ap.add_argument("--ref-paths", type=int, default=512, help="oracle paths per scheme per step")
-    ap.add_argument("--schemes", default="picard,full")
+    ap.add_argument("--schemes", default="picard,full,mlp")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -210,6 +210,21 @@ def main():
     x, W = lll.lll_build_nig_quadrature(wl.alpha, wl.beta, wl.dbar, wl.a, wl.Q)
     sims = {s: lll.LevyLibor(wl, x, W, stream=stream) for s in schemes}
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    mlp_info = None
+    mlp_params = None
+    if "mlp" in schemes:
+        # The learned compensator is trained once, on its own paths (seed 7),
+        # with the project's GPU kernels; the timed steps then price with it.
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss = lll.lll_mlp_train(sims["mlp"].ctx, hidden=128, layers=3, train_paths=1 << 16,
+                                 records_per_path=8, epochs=4, batch=8192, lr=2e-3, lr_final=1e-4, seed=7)
+        torch.cuda.synchronize()
+        n_params, in_dim, in_pad, _ = lll.lll_mlp_layout(sims["mlp"].ctx, 3)
+        mlp_params = lll.lll_mlp_params(sims["mlp"].ctx, 0, count=n_params)
+        mlp_info = {"train_s": time.perf_counter() - t0, "final_loss_scaled": loss, "params": int(n_params),
+                    "arch": f"{in_dim}->128x3->1 SiLU, BF16 weights, FP32 accumulate",
+                    "train_pairs": "2^16 paths x 8 recorded steps x live rates (~1e7)"}
 
     def one_step(evs=None):
         for i, s in enumerate(schemes):
@@ -231,6 +246,7 @@ def main():
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")  # profilers can select the timed launches
     for k in range(args.steps):
         flush.fill_(k & 0xFF)  # L2 flush between timed steps (outside the events)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in schemes]
@@ -242,6 +258,7 @@ def main():
             per_scheme_ms[s].append(ms)
             tot += ms
         step_ms.append(tot)
+    torch.cuda.nvtx.range_pop()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -267,28 +284,51 @@ def main():
         pp, _ = sims["picard"].prices()
         pf, _ = sims["full"].prices()
         per["picard_vs_full_max_bp"] = float(np.abs(pp - pf).max() * 1e4)
+    if "mlp" in per and "full" in per:
+        pm, _ = sims["mlp"].prices()
+        pf, _ = sims["full"].prices()
+        per["mlp_vs_full_max_bp"] = float(np.abs(pm - pf).max() * 1e4)
 
-    # roofline of the dominant kernel: the quadrature sweep costs 3Q FP32
-    # lane-ops per unit (one FMA into A, one multiply w*E, one FMA into P)
-    dom = max(schemes, key=lambda s: statistics.mean(per_scheme_ms[s]))
+    # Rooflines.  Quadrature kernels: 3Q FP32 lane-ops per unit (one FMA into
+    # A, one multiply w*E, one FMA into P) against 128 FP32 lanes per SM.
+    # MLP kernel: 2 x (multiply-adds of the network) per unit on the BF16
+    # tensor cores, against the measured sustained BF16 rate.
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sms * 128 * sm_max * 1e6 / 1e12
-    dom_ms = statistics.mean(per_scheme_ms[dom])
-    ops = wl.paths * wl.units_per_path() * 3 * wl.Q
-    achieved = ops / (dom_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFP32-lane-op/s",
-                "frac": achieved / peak, "traffic": None, "kernel": f"path_kernel<{dom}, QP={wl.Q}>",
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (MEASURED_PEAKS sm_max_mhz)"}
-    if clocks and clocks.get("sm_mhz"):
-        roofline["frac_at_sampled_clock"] = achieved / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+    fp32_peak = sms * 128 * sm_max * 1e6 / 1e12
+    units = wl.paths * wl.units_per_path()
+
+    def quad_roofline(s):
+        ms = statistics.mean(per_scheme_ms[s])
+        ach = units * 3 * wl.Q / (ms * 1e-3) / 1e12
+        r = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFP32-lane-op/s",
+             "frac": ach / fp32_peak, "traffic": None, "kernel": f"{s} path kernel, QP={wl.Q}",
+             "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS)"}
+        if clocks and clocks.get("sm_mhz"):
+            r["frac_at_sampled_clock"] = ach / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+        return r
+
+    def mlp_roofline():
+        ms = statistics.mean(per_scheme_ms["mlp"])
+        in_pad = 48 if wl.N + 3 <= 48 else 64
+        macs = in_pad * 128 + 128 * 128 * 2 + 128
+        ach = units * 2 * macs / (ms * 1e-3) / 1e12
+        peak = float(peaks.get("bf16_tflops_sustained", 1679.9))
+        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None, "kernel": "mlp path kernel (mma.sync bf16)",
+                "peak_basis": "bf16_tflops_sustained of MEASURED_PEAKS"}
+
+    dom = max(schemes, key=lambda s: statistics.mean(per_scheme_ms[s]))
+    roofline = mlp_roofline() if dom == "mlp" else quad_roofline(dom)
 
     # end to end through the C ABI from host arrays: init (H2D of the model
     # inputs, FP64 tables on the GPU), strikes, each scheme, prices (D2H).
     e2e = None
     if not args.no_e2e:
         h2d = (wl.L0.nbytes + wl.lam.nbytes + x.nbytes + W.nbytes) * len(schemes) + wl.strikes.nbytes * len(schemes)
+        if mlp_params is not None:
+            h2d += mlp_params[0].nbytes + mlp_params[1].nbytes
         d2h = len(schemes) * 2 * n * ns * 8
         ts = []
         for k in range(max(2, args.steps)):
@@ -296,6 +336,9 @@ def main():
             t0 = time.perf_counter()
             for s in schemes:
                 sim = lll.LevyLibor(wl, x, W, stream=stream)
+                if s == "mlp":
+                    lll.lll_mlp_init(sim.ctx, 128, 3, 0)
+                    lll.lll_mlp_params(sim.ctx, 1, mlp_params[0], scales=mlp_params[1])
                 lll.lll_simulate(sim.ctx, lll.SCHEMES[s], first, wl.paths, wl.seed)
                 sim.prices()
                 sim.close()
@@ -308,7 +351,7 @@ def main():
             et = float(t.item())
         e2e = {"value": units_per_step / et, "unit": "path·tenor·steps/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "note": "lll_init + lll_set_strikes + lll_simulate + lll_price_caplets + lll_destroy per scheme"}
+               "note": "per scheme: lll_init + lll_set_strikes (+ network parameters for mlp) + lll_simulate + lll_price_caplets + lll_destroy"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -322,7 +365,9 @@ def main():
                 "config": {"workload": _describe(wl, schemes), "global_paths": wl.paths * world,
                            "parallelism": f"path shards x{world}", "l2": "flushed between timed steps "
                            f"({L2_FLUSH_BYTES >> 20} MiB write outside the events)"},
-                "per_scheme": per, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "per_scheme": per, "roofline": roofline,
+                "roofline_picard": quad_roofline("picard") if "picard" in schemes else None,
+                "mlp": mlp_info, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": 2 * len(schemes) * args.steps}
         print(json.dumps(line), flush=True)
     for s in sims.values():

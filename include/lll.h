@@ -126,11 +126,13 @@ int lll_get_paths(lll_ctx *ctx, uint64_t first, uint64_t count, float *out);
 /* lll_set_launch -- override the launch shape of the path kernels:
  * threads per block (32..256, multiple of 32), resident blocks per SM
  * (0 = occupancy maximum), table rows staged per pipeline chunk (>= 1),
- * paths carried per thread (1 or 2; 2 is compiled for Q <= 64 only and
- * shares each staged table load between two paths).  0 for any argument
- * selects the library default. */
+ * paths carried per thread (1 or 2, one-lane mapping only; 2 is compiled for
+ * Q <= 64 and shares each staged table load between two paths), lanes per
+ * path (1: one lane sweeps all nodes of its path; 2 or 4: a group of that
+ * many lanes shares the node sweep of as many paths, full and Picard with the
+ * NIG driver).  0 for any argument selects the library default. */
 int lll_set_launch(lll_ctx *ctx, int threads_per_block, int blocks_per_sm, int chunk_rows,
-                   int paths_per_thread);
+                   int paths_per_thread, int lanes_per_path);
 
 /* lll_kernel_ms -- device time of the last simulation's path kernel and of the
  * whole lll_simulate call, from CUDA events on the context's stream.
@@ -165,6 +167,56 @@ int lll_simulate_noalloc(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t
  * gives only kappa, Section 4).  Host computation in FP64.
  *   nodes, weights: [Q] outputs, Q in [1, 128]. */
 int lll_build_nig_quadrature(lll_nig nig, double xmax, int Q, double *nodes, double *weights);
+
+/* ---- Batches of independent term structures -------------------------------
+ * Many models (uneven tenor counts, curves, volatilities, NIG parameters,
+ * strike grids and path budgets) simulated by one persistent launch whose
+ * tiles are balanced by cost across the SMs.  Instance q draws its increments
+ * from Philox counter (k, q, p_lo, p_hi): independent streams per instance.
+ * All instances must use the NIG driver and the same padded Q (16, 32, 64, 96
+ * or 128). */
+typedef struct {
+    int N;                 /* accrual dates (as lll_init) */
+    double tenor_delta;
+    const double *L0;      /* [N] */
+    int steps_per_period;
+    const double *lambda;  /* [n*s][n] */
+    int driver;            /* LLL_DRIVER_NIG */
+    lll_nig nig;
+    int Q;
+    const double *nodes, *weights; /* [Q] */
+    int n_strikes;
+    const double *strikes; /* [n][n_strikes] */
+    uint64_t paths;        /* > 0 */
+} lll_instance;
+
+typedef struct lll_batch lll_batch;
+
+/* lll_batch_init -- build every instance (FP64 tables on the GPU, as lll_init;
+ * an instance's LLL_EDOMAIN warning is accepted).  Inputs are copied. */
+int lll_batch_init(lll_batch **out, int n_inst, const lll_instance *inst, void *cuda_stream);
+
+/* lll_batch_set_launch -- threads per block, blocks per SM (0: occupancy
+ * maximum), table rows per staged chunk (0: default). */
+int lll_batch_set_launch(lll_batch *b, int threads_per_block, int blocks_per_sm, int chunk_rows);
+
+/* lll_batch_use_graph -- enable: the first simulation of a scheme captures
+ * its launch sequence (descriptor upload from pinned memory, batch kernel,
+ * final reduction) in a CUDA graph; later ones replay it. */
+int lll_batch_use_graph(lll_batch *b, int enable);
+
+/* lll_batch_simulate -- all instances, scheme LLL_FULL or LLL_PICARD, one
+ * launch.  Asynchronous. */
+int lll_batch_simulate(lll_batch *b, int scheme, uint64_t seed);
+
+/* lll_batch_prices -- caplet prices and standard errors of instance q
+ * ([n_q][n_strikes_q]).  Synchronises the stream. */
+int lll_batch_prices(lll_batch *b, int q, double *prices, double *stderr_);
+
+/* lll_batch_kernel_ms -- device time of the last lll_batch_simulate. */
+int lll_batch_kernel_ms(lll_batch *b, float *ms);
+
+void lll_batch_destroy(lll_batch *b);
 
 /* ---- Learned compensator (the MLP drift of LLL_MLP) -----------------------
  * A SiLU multilayer perceptron stands in for the jump integral of

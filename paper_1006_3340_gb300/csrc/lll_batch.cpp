@@ -1,0 +1,374 @@
+// lll_batch.cpp -- many independent term structures in one persistent launch
+// (C ABI lll_batch_*).
+//
+// Each instance is an ordinary model context (lll_init builds its FP64 tables
+// on the GPU).  A simulation of the batch is one launch of batch_kernel: the
+// tiles of all instances, in instance order, are cut into one contiguous range
+// per resident block of nearly equal cost (cost of a tile = its paths times
+// s n (n+1) / 2 units), so uneven instances (N from 8 to 80, path budgets from
+// 2^12 to 2^18) keep every SM busy to the end.  A block writes one partial per
+// instance it touched; a second kernel adds the partials of each instance in
+// block order, so results are deterministic.  The launch sequence can be
+// captured once in a CUDA graph and replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lll.h"
+#include "lll_ctx.h"
+#include "lll_internal.h"
+
+namespace lll {
+int batch_finalize(const double *partials, const size_t *seg_off, const int *inst_seg_ptr,
+                   const int *inst_segs, const size_t *out_off, int n_inst, const int *out_count,
+                   double *sums, cudaStream_t st);
+}
+
+using namespace lll;
+
+struct lll_batch {
+    std::vector<lll_ctx *> inst;
+    std::vector<uint64_t> paths;
+    cudaStream_t stream = nullptr;
+    int sm_count = 0, QP = 0, n_max = 0, ns_max = 0, threads = 128, blocks_per_sm = 0, chunk_rows = 0;
+    // device schedule
+    PathArgs *d_desc = nullptr;
+    PathArgs *h_desc = nullptr; // pinned: descriptors of the next launch
+    int *d_tile_inst = nullptr, *d_range = nullptr, *d_seg_first = nullptr;
+    uint32_t *d_tile_idx = nullptr;
+    size_t *d_seg_off = nullptr;
+    int *d_inst_seg_ptr = nullptr, *d_inst_segs = nullptr, *d_out_count = nullptr;
+    size_t *d_out_off = nullptr;
+    double *d_partials = nullptr, *d_sums = nullptr;
+    float *d_state = nullptr;
+    int grid = 0, scheme = -1;
+    size_t smem = 0, n_out_total = 0;
+    std::vector<size_t> out_off;
+    bool simulated = false, use_graph = false;
+    cudaGraphExec_t graph = nullptr;
+    int graph_scheme = -1;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    std::string err;
+};
+
+namespace {
+
+int berr(lll_batch *b, int code, const std::string &m)
+{
+    if (b) b->err = m;
+    record_error(nullptr, code, m.c_str());
+    return code;
+}
+
+void free_schedule(lll_batch *b)
+{
+    cudaFree(b->d_desc); cudaFree(b->d_tile_inst); cudaFree(b->d_range); cudaFree(b->d_seg_first);
+    cudaFree(b->d_tile_idx); cudaFree(b->d_seg_off); cudaFree(b->d_inst_seg_ptr); cudaFree(b->d_inst_segs);
+    cudaFree(b->d_out_count); cudaFree(b->d_out_off); cudaFree(b->d_partials); cudaFree(b->d_state);
+    b->d_desc = nullptr; b->d_tile_inst = b->d_range = b->d_seg_first = nullptr; b->d_tile_idx = nullptr;
+    b->d_seg_off = nullptr; b->d_inst_seg_ptr = b->d_inst_segs = b->d_out_count = nullptr;
+    b->d_out_off = nullptr; b->d_partials = nullptr; b->d_state = nullptr;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_scheme = -1;
+    b->scheme = -1;
+}
+
+template <class T>
+cudaError_t upload(T **d, const std::vector<T> &h, cudaStream_t st)
+{
+    cudaError_t e = cudaMalloc((void **)d, sizeof(T) * std::max<size_t>(h.size(), 1));
+    if (e != cudaSuccess) return e;
+    if (!h.empty()) e = cudaMemcpyAsync(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st);
+    return e;
+}
+
+// Build the tile schedule of `scheme` (if not built for it yet).
+int build_schedule(lll_batch *b, int scheme)
+{
+    if (b->scheme == scheme) return LLL_OK;
+    free_schedule(b);
+    const int T = b->threads;
+    const int CH = b->chunk_rows > 0 ? b->chunk_rows : std::min(b->n_max, std::max(1, (48 * 1024) / (2 * (b->QP / 2) * 16)));
+    const int nst = scheme == LLL_PICARD ? 2 : 1;
+    // smem as for the path kernel, sized for the largest instance
+    size_t smem = path_kernel_smem(b->QP, b->n_max, b->ns_max, T, CH);
+    if (smem > 227 * 1024) return berr(b, LLL_EUNSUPPORTED, "batch shared memory exceeds 227 KB");
+    int occ = 0;
+    cudaError_t e = (cudaError_t)batch_kernel_prepare(scheme, b->QP, smem, T, &occ);
+    if (e != cudaSuccess) return berr(b, LLL_ECUDA, std::string("batch kernel attributes: ") + cudaGetErrorString(e));
+    if (occ < 1) return berr(b, LLL_EUNSUPPORTED, "batch kernel does not fit on an SM");
+    const int bps = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, occ) : occ;
+    // tiles in instance order with their costs
+    const int ni = (int)b->inst.size();
+    std::vector<int> tile_inst;
+    std::vector<uint32_t> tile_idx;
+    std::vector<double> cost;
+    for (int q = 0; q < ni; ++q) {
+        const lll_ctx *c = b->inst[q];
+        const uint64_t nt = (b->paths[q] + T - 1) / T;
+        const double cu = (double)c->s * c->n * (c->n + 1) / 2.0;
+        for (uint64_t t = 0; t < nt; ++t) {
+            tile_inst.push_back(q);
+            tile_idx.push_back((uint32_t)t);
+            const uint64_t live = std::min<uint64_t>((uint64_t)T, b->paths[q] - t * T);
+            cost.push_back(cu * (double)live + 1.0);
+        }
+    }
+    const int ntiles = (int)tile_inst.size();
+    const int grid = std::max(1, std::min(ntiles, bps * b->sm_count));
+    double total = 0.0;
+    for (double c : cost) total += c;
+    std::vector<int> range(grid + 1, ntiles);
+    range[0] = 0;
+    {
+        double acc = 0.0;
+        int g = 1;
+        for (int t = 0; t < ntiles && g < grid; ++t) {
+            acc += cost[t];
+            while (g < grid && acc >= total * g / grid) range[g++] = t + 1;
+        }
+        for (int gg = 1; gg <= grid; ++gg) range[gg] = std::max(range[gg], range[gg - 1]);
+        range[grid] = ntiles;
+    }
+    // segments: one per (block, instance touched), in block order
+    std::vector<int> seg_first(grid, 0), seg_inst;
+    for (int g = 0; g < grid; ++g) {
+        seg_first[g] = (int)seg_inst.size();
+        int cur = -1;
+        for (int t = range[g]; t < range[g + 1]; ++t)
+            if (tile_inst[t] != cur) { cur = tile_inst[t]; seg_inst.push_back(cur); }
+    }
+    std::vector<size_t> seg_off(seg_inst.size());
+    size_t off = 0;
+    for (size_t sg = 0; sg < seg_inst.size(); ++sg) {
+        seg_off[sg] = off;
+        const lll_ctx *c = b->inst[seg_inst[sg]];
+        off += (size_t)c->n * c->ns * 2;
+    }
+    // per instance: its segments in block order, and its output offset
+    std::vector<int> inst_seg_ptr(ni + 1, 0), inst_segs, out_count(ni);
+    std::vector<std::vector<int>> lists(ni);
+    for (size_t sg = 0; sg < seg_inst.size(); ++sg) lists[seg_inst[sg]].push_back((int)sg);
+    b->out_off.assign(ni, 0);
+    size_t oo = 0;
+    for (int q = 0; q < ni; ++q) {
+        inst_seg_ptr[q] = (int)inst_segs.size();
+        inst_segs.insert(inst_segs.end(), lists[q].begin(), lists[q].end());
+        b->out_off[q] = oo;
+        out_count[q] = b->inst[q]->n * b->inst[q]->ns * 2;
+        oo += out_count[q];
+    }
+    inst_seg_ptr[ni] = (int)inst_segs.size();
+    b->n_out_total = oo;
+    cudaStream_t st = b->stream;
+    bool ok = upload(&b->d_tile_inst, tile_inst, st) == cudaSuccess && upload(&b->d_tile_idx, tile_idx, st) == cudaSuccess &&
+              upload(&b->d_range, range, st) == cudaSuccess && upload(&b->d_seg_first, seg_first, st) == cudaSuccess &&
+              upload(&b->d_seg_off, seg_off, st) == cudaSuccess && upload(&b->d_inst_seg_ptr, inst_seg_ptr, st) == cudaSuccess &&
+              upload(&b->d_inst_segs, inst_segs, st) == cudaSuccess && upload(&b->d_out_count, out_count, st) == cudaSuccess &&
+              upload(&b->d_out_off, b->out_off, st) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&b->d_partials, sizeof(double) * std::max<size_t>(off, 1)) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&b->d_state, sizeof(float) * (size_t)grid * nst * b->n_max * T) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&b->d_desc, sizeof(PathArgs) * ni) == cudaSuccess;
+    if (!b->d_sums) ok = ok && cudaMalloc((void **)&b->d_sums, sizeof(double) * std::max<size_t>(oo, 1)) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(st) == cudaSuccess;
+    if (!ok) {
+        free_schedule(b);
+        return berr(b, LLL_ENOMEM, "batch schedule buffers");
+    }
+    for (int q = 0; q < ni; ++q) b->inst[q]->chunk_rows = CH;
+    b->grid = grid;
+    b->smem = smem;
+    b->scheme = scheme;
+    return LLL_OK;
+}
+
+int launch_all(lll_batch *b)
+{
+    BatchArgs a{};
+    a.desc = b->d_desc; a.tile_inst = b->d_tile_inst; a.tile_idx = b->d_tile_idx; a.range = b->d_range;
+    a.seg_first = b->d_seg_first; a.seg_off = b->d_seg_off; a.partials = b->d_partials; a.state = b->d_state;
+    a.n_max = b->n_max; a.ns_max = b->ns_max;
+    a.chunk_rows = b->inst[0]->chunk_rows;
+    cudaStream_t st = b->stream;
+    cudaError_t e = cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(PathArgs) * b->inst.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return (int)e;
+    e = (cudaError_t)launch_batch_kernel(b->scheme, b->QP, b->grid, b->threads, b->smem, st, a);
+    if (e != cudaSuccess) return (int)e;
+    return batch_finalize(b->d_partials, b->d_seg_off, b->d_inst_seg_ptr, b->d_inst_segs, b->d_out_off,
+                          (int)b->inst.size(), b->d_out_count, b->d_sums, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int lll_batch_init(lll_batch **out, int n_inst, const lll_instance *inst, void *cuda_stream)
+{
+    if (!out || n_inst < 1 || !inst) return berr(nullptr, LLL_EINVAL, "need out, n_inst >= 1 and instances");
+    *out = nullptr;
+    lll_batch *b = new lll_batch();
+    b->stream = (cudaStream_t)cuda_stream;
+    for (int q = 0; q < n_inst; ++q) {
+        const lll_instance &I = inst[q];
+        lll_ctx *c = nullptr;
+        int rc = lll_init(&c, I.N, I.tenor_delta, I.L0, I.steps_per_period, I.lambda, I.driver, I.nig, I.Q,
+                          I.nodes, I.weights, cuda_stream);
+        if (rc != LLL_OK && rc != LLL_EDOMAIN) {
+            std::string m = std::string("instance ") + std::to_string(q) + ": " + lll_last_error(nullptr);
+            lll_batch_destroy(b);
+            return berr(nullptr, rc, m);
+        }
+        b->inst.push_back(c);
+        rc = lll_set_strikes(c, I.n_strikes, I.strikes);
+        if (rc == LLL_OK && I.paths == 0) rc = LLL_EINVAL;
+        if (rc != LLL_OK) {
+            std::string m = std::string("instance ") + std::to_string(q) + ": strikes or paths invalid";
+            lll_batch_destroy(b);
+            return berr(nullptr, LLL_EINVAL, m);
+        }
+        b->paths.push_back(I.paths);
+        if (q == 0) b->QP = c->QP;
+        if (c->QP != b->QP || c->driver != LLL_DRIVER_NIG) {
+            lll_batch_destroy(b);
+            return berr(nullptr, LLL_EUNSUPPORTED, "batched instances must share the NIG driver and padded Q");
+        }
+        b->n_max = std::max(b->n_max, c->n);
+        b->ns_max = std::max(b->ns_max, c->ns);
+    }
+    b->sm_count = b->inst[0]->sm_count;
+    if (cudaMallocHost((void **)&b->h_desc, sizeof(PathArgs) * n_inst) != cudaSuccess ||
+        cudaEventCreate(&b->ev[0]) != cudaSuccess || cudaEventCreate(&b->ev[1]) != cudaSuccess) {
+        lll_batch_destroy(b);
+        return berr(nullptr, LLL_ENOMEM, "pinned descriptor buffer or events");
+    }
+    *out = b;
+    return LLL_OK;
+}
+
+int lll_batch_set_launch(lll_batch *b, int threads_per_block, int blocks_per_sm, int chunk_rows)
+{
+    if (!b) return berr(nullptr, LLL_EINVAL, "batch is NULL");
+    if (threads_per_block != 0 && (threads_per_block < 32 || threads_per_block > kMaxThreads || threads_per_block % 32))
+        return berr(b, LLL_EINVAL, "threads_per_block must be a multiple of 32 in [32, 256]");
+    if (blocks_per_sm < 0 || chunk_rows < 0) return berr(b, LLL_EINVAL, "negative launch value");
+    b->threads = threads_per_block ? threads_per_block : 128;
+    b->blocks_per_sm = blocks_per_sm;
+    b->chunk_rows = chunk_rows;
+    free_schedule(b);
+    return LLL_OK;
+}
+
+int lll_batch_use_graph(lll_batch *b, int enable)
+{
+    if (!b) return berr(nullptr, LLL_EINVAL, "batch is NULL");
+    b->use_graph = enable != 0;
+    return LLL_OK;
+}
+
+int lll_batch_simulate(lll_batch *b, int scheme, uint64_t seed)
+{
+    if (!b) return berr(nullptr, LLL_EINVAL, "batch is NULL");
+    if (scheme != LLL_FULL && scheme != LLL_PICARD)
+        return berr(b, LLL_EINVAL, "the batched launch runs the full or the Picard scheme");
+    if (!batch_kernel_supported(scheme, b->QP)) return berr(b, LLL_EUNSUPPORTED, "no batch kernel for this Q");
+    int rc = build_schedule(b, scheme);
+    if (rc != LLL_OK) return rc;
+    // the previous launch may still read the pinned descriptors
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return berr(b, LLL_ECUDA, "stream synchronize");
+    for (size_t q = 0; q < b->inst.size(); ++q) {
+        LaunchPlan plan;
+        b->inst[q]->lpp = 1;
+        b->inst[q]->ppt = 1;
+        rc = plan_launch(b->inst[q], scheme, 0, b->paths[q], seed, &plan);
+        if (rc != LLL_OK) return berr(b, rc, std::string("instance plan: ") + lll_last_error(b->inst[q]));
+        plan.args.inst = (uint32_t)q; // Philox counter word 1: instances draw independent streams
+        b->h_desc[q] = plan.args;
+    }
+    cudaStream_t st = b->stream;
+    cudaError_t e = cudaEventRecord(b->ev[0], st);
+    if (e == cudaSuccess) {
+        if (b->use_graph) {
+            if (!b->graph || b->graph_scheme != scheme) {
+                if (b->graph) cudaGraphExecDestroy(b->graph);
+                b->graph = nullptr;
+                cudaGraph_t g = nullptr;
+                cudaStream_t cap = nullptr;
+                e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+                if (e == cudaSuccess) e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaStream_t keep = b->stream;
+                    b->stream = cap;
+                    const int lr = launch_all(b);
+                    b->stream = keep;
+                    e = cudaStreamEndCapture(cap, &g);
+                    if (e == cudaSuccess && lr != 0) e = (cudaError_t)lr;
+                }
+                if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+                if (g) cudaGraphDestroy(g);
+                if (cap) cudaStreamDestroy(cap);
+                b->graph_scheme = scheme;
+            }
+            if (e == cudaSuccess) e = cudaGraphLaunch(b->graph, st);
+        } else {
+            e = (cudaError_t)launch_all(b);
+        }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev[1], st);
+    if (e != cudaSuccess) return berr(b, LLL_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+    b->simulated = true;
+    return LLL_OK;
+}
+
+int lll_batch_prices(lll_batch *b, int q, double *prices, double *stderr_)
+{
+    if (!b) return berr(nullptr, LLL_EINVAL, "batch is NULL");
+    if (!b->simulated) return berr(b, LLL_ESTATE, "no batch simulation to read");
+    if (q < 0 || q >= (int)b->inst.size() || !prices) return berr(b, LLL_EINVAL, "bad instance or output");
+    const lll_ctx *c = b->inst[q];
+    const size_t cnt = (size_t)c->n * c->ns;
+    std::vector<double> buf(2 * cnt);
+    if (cudaMemcpyAsync(buf.data(), b->d_sums + b->out_off[q], sizeof(double) * 2 * cnt, cudaMemcpyDeviceToHost,
+                        b->stream) != cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return berr(b, LLL_ECUDA, "reading batch sums");
+    const double P = (double)b->paths[q];
+    for (size_t e = 0; e < cnt; ++e) {
+        const double mean = buf[2 * e] / P;
+        prices[e] = mean;
+        if (stderr_) {
+            const double var = std::max(buf[2 * e + 1] / P - mean * mean, 0.0) * P / std::max(P - 1.0, 1.0);
+            stderr_[e] = std::sqrt(var / P);
+        }
+    }
+    return LLL_OK;
+}
+
+int lll_batch_kernel_ms(lll_batch *b, float *ms)
+{
+    if (!b || !ms) return berr(b, LLL_EINVAL, "batch or output is NULL");
+    if (!b->simulated) return berr(b, LLL_ESTATE, "no batch simulation timed");
+    if (cudaEventSynchronize(b->ev[1]) != cudaSuccess || cudaEventElapsedTime(ms, b->ev[0], b->ev[1]) != cudaSuccess)
+        return berr(b, LLL_ECUDA, "batch timing");
+    return LLL_OK;
+}
+
+void lll_batch_destroy(lll_batch *b)
+{
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    else cudaDeviceSynchronize();
+    free_schedule(b);
+    cudaFree(b->d_sums);
+    if (b->h_desc) cudaFreeHost(b->h_desc);
+    for (auto &e : b->ev)
+        if (e) cudaEventDestroy(e);
+    for (lll_ctx *c : b->inst) lll_destroy(c);
+    delete b;
+}
+
+}  // extern "C"

@@ -85,6 +85,13 @@ namespace lll {
 
 int record_error(lll_ctx *ctx, int code, const char *msg) { return fail(ctx, code, msg); }
 
+int launch_plan(const LaunchPlan &plan, const PathArgs &a)
+{
+    if (plan.lpp > 1)
+        return launch_group_kernel(plan.scheme, plan.qp, plan.lpp, plan.grid, plan.threads, plan.smem, plan.stream, a);
+    return launch_path_kernel(plan.scheme, plan.qp, plan.ppt, plan.grid, plan.threads, plan.smem, plan.stream, a);
+}
+
 // Same launch shape and arguments as lll_simulate, with no allocation: the
 // per-block scratch sizes are returned for the caller to place.
 int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, uint64_t seed,
@@ -99,17 +106,29 @@ int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, u
     if (paths == 0) return fail(ctx, LLL_EINVAL, "paths must be > 0");
     if (first_path + paths < first_path) return fail(ctx, LLL_EINVAL, "path range overflows");
     const int QPk = (scheme == LLL_FROZEN) ? 0 : ctx->QP;
-    const int R = ctx->ppt > 0 ? ctx->ppt : 1;
-    if (!path_kernel_supported(scheme, QPk, R))
+    // Lanes per group of paths: 1 (one lane sweeps all nodes of its path) or
+    // 2 / 4 (lane groups share the node sweep); the default is 1.
+    const int lpp = ctx->lpp > 0 ? ctx->lpp : 1;
+    const int R = lpp > 1 ? 1 : (ctx->ppt > 0 ? ctx->ppt : 1);
+    if (lpp > 1 && !group_kernel_supported(scheme, QPk, lpp))
+        return fail(ctx, LLL_EUNSUPPORTED, "lane groups need a node table (NIG, full or Picard)");
+    if (lpp == 1 && !path_kernel_supported(scheme, QPk, R))
         return fail(ctx, LLL_EUNSUPPORTED, "no kernel for this Q and paths per thread");
     const int T = ctx->threads, CH = ctx->chunk_rows;
-    const size_t smem = path_kernel_smem(QPk, ctx->n, ctx->ns, T, CH);
+    const size_t smem = lpp > 1 ? group_kernel_smem(QPk, ctx->n, ctx->ns, T, CH)
+                                : path_kernel_smem(QPk, ctx->n, ctx->ns, T, CH);
     if (smem > 227 * 1024) return fail(ctx, LLL_EUNSUPPORTED, "shared memory need exceeds 227 KB");
-    cudaError_t e = (cudaError_t)path_kernel_prepare(scheme, QPk, R, smem);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
     int occ = 0;
-    e = (cudaError_t)path_kernel_occupancy(scheme, QPk, R, T, smem, &occ);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
+    cudaError_t e;
+    if (lpp > 1) {
+        e = (cudaError_t)group_kernel_prepare(scheme, QPk, lpp, smem, T, &occ);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "group kernel attributes");
+    } else {
+        e = (cudaError_t)path_kernel_prepare(scheme, QPk, R, smem);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
+        e = (cudaError_t)path_kernel_occupancy(scheme, QPk, R, T, smem, &occ);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");
+    }
     if (occ < 1) return fail(ctx, LLL_EUNSUPPORTED, "launch shape does not fit on an SM");
     const int bps = ctx->blocks_per_sm > 0 ? std::min(ctx->blocks_per_sm, occ) : occ;
     const uint64_t tiles = (paths + (uint64_t)T * R - 1) / ((uint64_t)T * R);
@@ -133,7 +152,7 @@ int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, u
         a.nig_beta = (float)ctx->nig.beta; a.nig_muh = (float)(ctx->mu * ctx->h);
     }
     plan->args = a;
-    plan->scheme = scheme; plan->qp = QPk; plan->ppt = R; plan->threads = T; plan->grid = grid;
+    plan->scheme = scheme; plan->qp = QPk; plan->ppt = R; plan->lpp = lpp; plan->threads = T; plan->grid = grid;
     plan->smem = smem;
     plan->state_floats_per_block = (size_t)R * nst * ctx->n * T;
     plan->partial_doubles_per_block = (size_t)ctx->n * ctx->ns * 2;
@@ -312,7 +331,7 @@ int lll_set_snapshots(lll_ctx *ctx, uint64_t count, uint64_t stride)
 }
 
 int lll_set_launch(lll_ctx *ctx, int threads_per_block, int blocks_per_sm, int chunk_rows,
-                   int paths_per_thread)
+                   int paths_per_thread, int lanes_per_path)
 {
     if (!ctx) return fail(nullptr, LLL_EINVAL, "ctx is NULL");
     if (threads_per_block != 0 &&
@@ -321,7 +340,10 @@ int lll_set_launch(lll_ctx *ctx, int threads_per_block, int blocks_per_sm, int c
     if (blocks_per_sm < 0 || chunk_rows < 0) return fail(ctx, LLL_EINVAL, "negative launch value");
     if (paths_per_thread < 0 || paths_per_thread > 2)
         return fail(ctx, LLL_EINVAL, "paths_per_thread must be 0 (automatic), 1 or 2");
+    if (lanes_per_path != 0 && lanes_per_path != 1 && lanes_per_path != 2 && lanes_per_path != 4)
+        return fail(ctx, LLL_EINVAL, "lanes_per_path must be 0 (default), 1, 2 or 4");
     ctx->ppt = paths_per_thread;
+    ctx->lpp = lanes_per_path;
     if (threads_per_block) ctx->threads = threads_per_block;
     ctx->blocks_per_sm = blocks_per_sm;
     ctx->chunk_rows = chunk_rows ? std::min(chunk_rows, ctx->n) : default_chunk_rows(ctx->n, ctx->QP);
@@ -371,7 +393,7 @@ int lll_simulate(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, 
     const size_t smem = plan.smem;
     cudaError_t e;
     CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
-    e = (cudaError_t)launch_path_kernel(scheme, QPk, plan.ppt, grid, T, smem, ctx->stream, a);
+    e = (cudaError_t)launch_plan(plan, a);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "path kernel launch");
     CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
     e = (cudaError_t)launch_finalize(ctx->d_partials, grid, (int)nout, ctx->d_sums, ctx->stream);

@@ -36,7 +36,7 @@ struct lll_ctx {
     bool simulated = false;
     uint64_t last_paths = 0;
     uint64_t last_snap_paths = 0;
-    int threads = 128, blocks_per_sm = 0, chunk_rows = 0, ppt = 0; // ppt 0: automatic
+    int threads = 128, blocks_per_sm = 0, chunk_rows = 0, ppt = 0, lpp = 0; // 0: automatic
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     std::vector<double> lam; // host copy of lambda [S][n]
     lll::MlpState *mlp = nullptr;

@@ -37,11 +37,24 @@ struct PathArgs {
     double ig_md, ig_ld;             // m and l in FP64 for the acceptance re-check
 };
 
+// Many instances in one persistent launch (see batch_kernel in lll_paths.cu).
+struct BatchArgs {
+    const PathArgs *desc;    // [n_inst] per-instance arguments (state/partials unused)
+    const int *tile_inst;    // [tiles] instance of each tile, instance-ordered
+    const uint32_t *tile_idx;// [tiles] tile index within its instance
+    const int *range;        // [grid+1] tile range of each block
+    const int *seg_first;    // [grid] first output segment of each block
+    const size_t *seg_off;   // [segments] offset (doubles) of each segment in partials
+    double *partials;        // segment outputs: [n][ns][2] per segment
+    float *state;            // [grid][NST][n_max][threads]
+    int n_max, ns_max, chunk_rows;
+};
+
 // The launch lll_simulate would make for one simulation, worked out without
 // allocating anything; state and partials are left for the caller to place.
 struct LaunchPlan {
     PathArgs args;
-    int scheme, qp, ppt, threads, grid;
+    int scheme, qp, ppt, lpp, threads, grid; // lpp: lanes per group of paths (1, 2 or 4)
     size_t smem;
     size_t state_floats_per_block, partial_doubles_per_block;
     int n_out; // doubles written by the final reduction: n * n_strikes * 2
@@ -57,6 +70,19 @@ int path_kernel_occupancy(int scheme, int QP, int R, int threads, size_t smem, i
 int path_kernel_prepare(int scheme, int QP, int R, size_t smem);
 bool path_kernel_supported(int scheme, int QP, int R);
 size_t path_kernel_smem(int QP, int n, int ns, int threads, int chunk_rows);
+
+// Launchers implemented in lll_paths_group.cu (four lanes per group of four paths).
+bool group_kernel_supported(int scheme, int QP, int G);
+size_t group_kernel_smem(int QP, int n, int ns, int threads, int chunk_rows);
+int group_kernel_prepare(int scheme, int QP, int G, size_t smem, int threads, int *blocks_per_sm);
+int launch_group_kernel(int scheme, int QP, int G, int grid, int threads, size_t smem, cudaStream_t st,
+                        const PathArgs &a);
+struct LaunchPlan;
+int launch_plan(const LaunchPlan &plan, const PathArgs &a);
+bool batch_kernel_supported(int scheme, int QP);
+int batch_kernel_prepare(int scheme, int QP, size_t smem, int threads, int *blocks_per_sm);
+int launch_batch_kernel(int scheme, int QP, int grid, int threads, size_t smem, cudaStream_t st,
+                        const BatchArgs &b);
 
 // Launchers implemented in lll_tables.cu.
 int launch_tables(const double *lam, const double *x, const double *W, int n, int S, int Q, int QP,

@@ -86,8 +86,7 @@ extern "C" int lll_simulate_noalloc(lll_ctx *ctx, int scheme, uint64_t first_pat
     PathArgs a = plan.args;
     a.state = static_cast<float *>(base);
     a.partials = reinterpret_cast<double *>(static_cast<unsigned char *>(base) + state_bytes);
-    e = (cudaError_t)launch_path_kernel(plan.scheme, plan.qp, plan.ppt, plan.grid, plan.threads,
-                                        plan.smem, plan.stream, a);
+    e = (cudaError_t)launch_plan(plan, a);
     if (e != cudaSuccess) {
         std::string msg = std::string("path kernel launch: ") + cudaGetErrorString(e);
         return record_error(ctx, LLL_ECUDA, msg.c_str());

@@ -51,6 +51,16 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// delta L / (1 + delta L) for x = log(delta L) (approximate ex2 and rcp: w only
+// scales the state-dependent part of the compensator).
+__device__ __forceinline__ float weight_of(float x)
+{
+    float e, r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(e) : "f"(-1.4426950408889634f * x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(1.0f + e));
+    return r;
+}
+
 __device__ __forceinline__ void kahan_add(double *s, double *c, double x)
 {
     const double y = x - *c;
@@ -122,27 +132,19 @@ __device__ __forceinline__ void issue_chunk(const PathArgs &a, const Smem &sm, i
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) cp_async16(sm.row + b * CH + e, a.row + r0 + e);
 }
 
+// One tile of T*R paths of the simulation `a`: all Euler steps, payoffs
+// accumulated into sm.bsum.  st: this thread's column of the block's state slot.
 template <int SCHEME, int QP, int R>
-__global__ void __launch_bounds__(kMaxThreads) path_kernel(const PathArgs a)
+__device__ __forceinline__ void run_tile(const PathArgs &a, const Smem &sm, float *st, uint64_t tile)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int Q2 = QP > 0 ? QP / 2 : 1;
     constexpr int NST = (SCHEME == PICARD) ? 2 : 1;
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = a.n, s = a.s, S = a.S, ns = a.ns, CH = a.chunk_rows;
-    const Smem sm = carve(smem_raw, QP, n, ns, T, CH);
-
-    for (int e = tid; e < n; e += T) sm.c0[e] = a.c0[e];
-    for (int e = tid; e < 4 * n * ns; e += T) sm.bsum[e] = 0.0;
-
-    // This block's state slot: [R][NST][n][T]; thread tid owns column tid.
-    float *st = a.state + (size_t)blockIdx.x * R * NST * n * T + tid;
     const size_t rs = (size_t)NST * n * T; // stride between the R paths of a thread
     const uint64_t TP = (uint64_t)T * R;   // paths per tile
-    const uint64_t ntiles = (a.paths + TP - 1) / TP;
     const float h = a.h, delta = a.delta;
-
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    {
         uint64_t lp[R], p[R], sidx[R];
         bool active[R];
 #pragma unroll
@@ -192,72 +194,67 @@ __global__ void __launch_bounds__(kMaxThreads) path_kernel(const PathArgs a)
                 const float4 *tb = sm.tab + (size_t)buf * CH * Q2;
                 const float4 *rb = sm.row + buf * CH;
                 // state of the first row; each row prefetches the next one's
-                float c0v[R], c1v[R];
+                // State and weight of the first row; every row then loads the
+                // next row's state and computes its weight, so that the MUFU
+                // latency of w overlaps with the current row's node sweep.
+                float c0v[R], c1v[R], wn[R];
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
                     c0v[q] = st[q * rs + (size_t)(itop - 1) * T];
                     c1v[q] = (NST == 2) ? st[q * rs + (size_t)(n + itop - 1) * T] : 0.0f;
+                    if (SCHEME != FROZEN)
+                        wn[q] = weight_of(sm.c0[itop - 1] + (SCHEME == PICARD ? rb[itop - ibot].z : 0.0f) + c0v[q]);
                 }
                 for (int i = itop; i >= ibot; --i) {
                     const int r = i - ibot;
                     const float4 rc = rb[r]; // lambda, K, D0, b0*h
-                    float v0[R], v1[R];
+                    float v0[R], v1[R], w[R];
 #pragma unroll
                     for (int q = 0; q < R; ++q) {
                         v0[q] = c0v[q];
                         v1[q] = c1v[q];
-                        if (i > ibot) {
+                        w[q] = wn[q];
+                    }
+                    if (i > ibot) {
+                        const float cxn = sm.c0[i - 2] + (SCHEME == PICARD ? rb[r - 1].z : 0.0f);
+#pragma unroll
+                        for (int q = 0; q < R; ++q) {
                             c0v[q] = st[q * rs + (size_t)(i - 2) * T];
                             if (NST == 2) c1v[q] = st[q * rs + (size_t)(n + i - 2) * T];
+                            if (SCHEME != FROZEN) wn[q] = weight_of(cxn + c0v[q]);
                         }
                     }
                     float bh[R];
                     if (SCHEME == FROZEN) {
 #pragma unroll
                         for (int q = 0; q < R; ++q) bh[q] = rc.w;
-                    } else {
-                        const float cx = sm.c0[i - 1];
-                        float w[R];
+                    } else if (QP > 0) {
+                        const float4 *tr = tb + (size_t)r * Q2;
+                        float2 acc[R][4];
+                        float2 w2[R];
+#pragma unroll
+                        for (int q = 0; q < R; ++q) w2[q] = make_float2(w[q], w[q]);
+#pragma unroll
+                        for (int j = 0; j < Q2; ++j) {
+                            const float4 v = tr[j];
+                            const float2 e2 = make_float2(v.x, v.y);
+                            const float2 a2 = make_float2(v.z, v.w);
+#pragma unroll
+                            for (int q = 0; q < R; ++q) {
+                                acc[q][j & 3] = (j < 4) ? __fmul2_rn(a2, P[q][j]) : __ffma2_rn(a2, P[q][j], acc[q][j & 3]);
+                                P[q][j] = __ffma2_rn(__fmul2_rn(w2[q], e2), P[q][j], P[q][j]);
+                            }
+                        }
 #pragma unroll
                         for (int q = 0; q < R; ++q) {
-                            const float zoff = (SCHEME == FULL) ? v0[q] : (rc.z + v0[q]);
-                            // delta L / (1 + delta L) with log(delta L) = cx + zoff
-                            w[q] = __frcp_rn(1.0f + __expf(-(cx + zoff)));
+                            const float2 s2 = __fadd2_rn(__fadd2_rn(acc[q][0], acc[q][1]), __fadd2_rn(acc[q][2], acc[q][3]));
+                            bh[q] = -(rc.y + (s2.x + s2.y)) * h;
                         }
-                        if (QP > 0) {
-                            const float4 *tr = tb + (size_t)r * Q2;
-                            float2 acc[R][4];
-                            float2 w2[R];
+                    } else {
 #pragma unroll
-                            for (int q = 0; q < R; ++q) {
-                                w2[q] = make_float2(w[q], w[q]);
-#pragma unroll
-                                for (int u = 0; u < 4; ++u) acc[q][u] = make_float2(0.0f, 0.0f);
-                            }
-#pragma unroll
-                            for (int j = 0; j < Q2; ++j) {
-                                const float4 v = tr[j];
-                                const float2 e2 = make_float2(v.x, v.y);
-                                const float2 a2 = make_float2(v.z, v.w);
-#pragma unroll
-                                for (int q = 0; q < R; ++q) {
-                                    acc[q][j & 3] = __ffma2_rn(a2, P[q][j], acc[q][j & 3]);
-                                    P[q][j] = __ffma2_rn(__fmul2_rn(w2[q], e2), P[q][j], P[q][j]);
-                                }
-                            }
-#pragma unroll
-                            for (int q = 0; q < R; ++q) {
-                                const float Ai =
-                                    rc.y + (((acc[q][0].x + acc[q][0].y) + (acc[q][1].x + acc[q][1].y)) +
-                                            ((acc[q][2].x + acc[q][2].y) + (acc[q][3].x + acc[q][3].y)));
-                                bh[q] = -Ai * h;
-                            }
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < R; ++q) {
-                                bh[q] = (-0.5f * rc.x * rc.x - rc.x * scont[q]) * h;
-                                scont[q] = fmaf(w[q], rc.x, scont[q]);
-                            }
+                        for (int q = 0; q < R; ++q) {
+                            bh[q] = (-0.5f * rc.x * rc.x - rc.x * scont[q]) * h;
+                            scont[q] = fmaf(w[q], rc.x, scont[q]);
                         }
                     }
 #pragma unroll
@@ -322,11 +319,73 @@ __global__ void __launch_bounds__(kMaxThreads) path_kernel(const PathArgs a)
         }
         cp_wait_0();
     }
+}
+
+template <int SCHEME, int QP, int R>
+__global__ void __launch_bounds__(kMaxThreads) path_kernel(const PathArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NST = (SCHEME == PICARD) ? 2 : 1;
+    const int T = blockDim.x, tid = threadIdx.x;
+    const int n = a.n, ns = a.ns;
+    const Smem sm = carve(smem_raw, QP, n, ns, T, a.chunk_rows);
+    for (int e = tid; e < n; e += T) sm.c0[e] = a.c0[e];
+    for (int e = tid; e < 4 * n * ns; e += T) sm.bsum[e] = 0.0;
+    // This block's state slot: [R][NST][n][T]; thread tid owns column tid.
+    float *st = a.state + (size_t)blockIdx.x * R * NST * n * T + tid;
+    const uint64_t ntiles = (a.paths + (uint64_t)T * R - 1) / ((uint64_t)T * R);
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) run_tile<SCHEME, QP, R>(a, sm, st, tile);
     __syncthreads();
     double *out = a.partials + (size_t)blockIdx.x * n * ns * 2;
     for (int e = tid; e < n * ns; e += T) {
         out[2 * e + 0] = sm.bsum[4 * e + 0];
         out[2 * e + 1] = sm.bsum[4 * e + 2];
+    }
+}
+
+// Many independent term structures in one persistent launch.  Block g
+// processes the tiles [range[g], range[g+1]) of a cost-balanced, instance-
+// ordered tile list; whenever it leaves an instance it writes that instance's
+// payoff partials to its own segment, so the final sums (per instance, over
+// segments in block order) are deterministic.
+template <int SCHEME, int QP>
+__global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchArgs b)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int NST = (SCHEME == PICARD) ? 2 : 1;
+    const int T = blockDim.x, tid = threadIdx.x;
+    const Smem sm = carve(smem_raw, QP, b.n_max, b.ns_max, T, b.chunk_rows);
+    float *st = b.state + (size_t)blockIdx.x * NST * b.n_max * T + tid;
+    int cur = -1, seg = b.seg_first[blockIdx.x];
+    __shared__ PathArgs sa; // the current instance's arguments
+    const PathArgs *a = &sa;
+    for (int t = b.range[blockIdx.x]; t < b.range[blockIdx.x + 1]; ++t) {
+        const int q = b.tile_inst[t];
+        if (q != cur) {
+            if (cur >= 0) {
+                __syncthreads();
+                double *out = b.partials + b.seg_off[seg++];
+                for (int e = tid; e < a->n * a->ns; e += T) {
+                    out[2 * e + 0] = sm.bsum[4 * e + 0];
+                    out[2 * e + 1] = sm.bsum[4 * e + 2];
+                }
+            }
+            cur = q;
+            __syncthreads();
+            if (tid == 0) sa = b.desc[q];
+            __syncthreads();
+            for (int e = tid; e < a->n; e += T) sm.c0[e] = a->c0[e];
+            for (int e = tid; e < 4 * a->n * a->ns; e += T) sm.bsum[e] = 0.0;
+        }
+        run_tile<SCHEME, QP, 1>(*a, sm, st, b.tile_idx[t]);
+    }
+    if (cur >= 0) {
+        __syncthreads();
+        double *out = b.partials + b.seg_off[seg];
+        for (int e = tid; e < a->n * a->ns; e += T) {
+            out[2 * e + 0] = sm.bsum[4 * e + 0];
+            out[2 * e + 1] = sm.bsum[4 * e + 2];
+        }
     }
 }
 
@@ -369,7 +428,54 @@ KernelFn pick(int scheme, int QP, int R)
     }
 }
 
+typedef void (*BatchFn)(const BatchArgs);
+
+BatchFn pick_batch(int scheme, int QP)
+{
+    if (scheme == PICARD) {
+        switch (QP) {
+        case 16: return batch_kernel<PICARD, 16>;
+        case 32: return batch_kernel<PICARD, 32>;
+        case 64: return batch_kernel<PICARD, 64>;
+        case 96: return batch_kernel<PICARD, 96>;
+        case 128: return batch_kernel<PICARD, 128>;
+        default: return nullptr;
+        }
+    }
+    if (scheme == FULL) {
+        switch (QP) {
+        case 16: return batch_kernel<FULL, 16>;
+        case 32: return batch_kernel<FULL, 32>;
+        case 64: return batch_kernel<FULL, 64>;
+        case 96: return batch_kernel<FULL, 96>;
+        case 128: return batch_kernel<FULL, 128>;
+        default: return nullptr;
+        }
+    }
+    return nullptr;
+}
+
 }  // namespace
+
+bool batch_kernel_supported(int scheme, int QP) { return pick_batch(scheme, QP) != nullptr; }
+
+int batch_kernel_prepare(int scheme, int QP, size_t smem, int threads, int *blocks_per_sm)
+{
+    BatchFn f = pick_batch(scheme, QP);
+    if (!f) return (int)cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, smem);
+}
+
+int launch_batch_kernel(int scheme, int QP, int grid, int threads, size_t smem, cudaStream_t st,
+                        const BatchArgs &b)
+{
+    BatchFn f = pick_batch(scheme, QP);
+    if (!f) return (int)cudaErrorInvalidValue;
+    f<<<grid, threads, smem, st>>>(b);
+    return (int)cudaGetLastError();
+}
 
 bool path_kernel_supported(int scheme, int QP, int R) { return pick(scheme, QP, R) != nullptr; }
 

@@ -105,7 +105,33 @@ __global__ void finalize_kernel(const double *partials, int grid, int n_out, dou
     sums[e] = s;
 }
 
+// Per instance of a batch: add its segment partials in block order.
+__global__ void batch_finalize_kernel(const double *partials, const size_t *seg_off, const int *inst_seg_ptr,
+                                      const int *inst_segs, const size_t *out_off, const int *out_count,
+                                      double *sums)
+{
+    const int q = blockIdx.x;
+    for (int e = threadIdx.x; e < out_count[q]; e += blockDim.x) {
+        double s = 0.0, c = 0.0;
+        for (int k = inst_seg_ptr[q]; k < inst_seg_ptr[q + 1]; ++k) {
+            const double y = partials[seg_off[inst_segs[k]] + e] - c;
+            const double t = s + y;
+            c = (t - s) - y;
+            s = t;
+        }
+        sums[out_off[q] + e] = s;
+    }
+}
+
 }  // namespace
+
+int batch_finalize(const double *partials, const size_t *seg_off, const int *inst_seg_ptr, const int *inst_segs,
+                   const size_t *out_off, int n_inst, const int *out_count, double *sums, cudaStream_t st)
+{
+    batch_finalize_kernel<<<n_inst, 128, 0, st>>>(partials, seg_off, inst_seg_ptr, inst_segs, out_off, out_count,
+                                                  sums);
+    return (int)cudaGetLastError();
+}
 
 int launch_tables(const double *lam, const double *x, const double *W, int n, int S, int Q, int QP,
                   float4 *tab, float4 *row, float *Ctab, cudaStream_t st)

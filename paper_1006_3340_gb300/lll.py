@@ -40,6 +40,13 @@ class lll_nig(ctypes.Structure):
                 ("delta", ctypes.c_double), ("mu", ctypes.c_double)]
 
 
+class lll_instance(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("tenor_delta", ctypes.c_double), ("L0", ctypes.c_void_p),
+                ("steps_per_period", ctypes.c_int), ("lambda_", ctypes.c_void_p), ("driver", ctypes.c_int),
+                ("nig", lll_nig), ("Q", ctypes.c_int), ("nodes", ctypes.c_void_p), ("weights", ctypes.c_void_p),
+                ("n_strikes", ctypes.c_int), ("strikes", ctypes.c_void_p), ("paths", ctypes.c_uint64)]
+
+
 _lib = None
 _dp = ctypes.POINTER(ctypes.c_double)
 _fp = ctypes.POINTER(ctypes.c_float)
@@ -68,7 +75,7 @@ def load():
         "lll_get_sums": (I, [V, _dp, _dp, ctypes.POINTER(U64)]),
         "lll_price_caplets": (I, [V, _dp, _dp]),
         "lll_get_paths": (I, [V, U64, U64, _fp]),
-        "lll_set_launch": (I, [V, I, I, I, I]),
+        "lll_set_launch": (I, [V, I, I, I, I, I]),
         "lll_kernel_ms": (I, [V, _fp, _fp]),
         "lll_build_nig_quadrature": (I, [lll_nig, ctypes.c_double, I, _dp, _dp]),
         "lll_mlp_init": (I, [V, I, I, U64]),
@@ -79,6 +86,13 @@ def load():
         "lll_mlp_eval": (I, [V, _fp, _fp, I, _fp, _fp, _dp]),
         "lll_mlp_save": (I, [V, ctypes.c_char_p]),
         "lll_mlp_load": (I, [V, ctypes.c_char_p]),
+        "lll_batch_init": (I, [ctypes.POINTER(V), I, ctypes.POINTER(lll_instance), V]),
+        "lll_batch_set_launch": (I, [V, I, I, I]),
+        "lll_batch_use_graph": (I, [V, I]),
+        "lll_batch_simulate": (I, [V, I, U64]),
+        "lll_batch_prices": (I, [V, I, _dp, _dp]),
+        "lll_batch_kernel_ms": (I, [V, _fp]),
+        "lll_batch_destroy": (None, [V]),
         "lll_last_error": (ctypes.c_char_p, [V]),
         "lll_destroy": (None, [V]),
     }
@@ -175,9 +189,9 @@ def lll_get_paths(ctx, n, first, count):
     return out
 
 
-def lll_set_launch(ctx, threads=0, blocks_per_sm=0, chunk_rows=0, paths_per_thread=0):
+def lll_set_launch(ctx, threads=0, blocks_per_sm=0, chunk_rows=0, paths_per_thread=0, lanes_per_path=0):
     _check(load().lll_set_launch(ctx, int(threads), int(blocks_per_sm), int(chunk_rows),
-                                 int(paths_per_thread)), ctx)
+                                 int(paths_per_thread), int(lanes_per_path)), ctx)
 
 
 def lll_kernel_ms(ctx):
@@ -243,6 +257,54 @@ def lll_mlp_load(ctx, path):
     _check(load().lll_mlp_load(ctx, str(path).encode()), ctx)
 
 
+def lll_batch_init(instances, stream: int = 0):
+    """instances: list of (workload, nodes, weights).  Returns (handle, keepalive)."""
+    lib = load()
+    keep = []
+    arr = (lll_instance * len(instances))()
+    for q, (wl, x, W) in enumerate(instances):
+        L0, lam, st = _f64(wl.L0), _f64(wl.lam), _f64(wl.strikes)
+        x, W = _f64(x), _f64(W)
+        keep += [L0, lam, st, x, W]
+        mu = float("nan") if wl.mu is None else float(wl.mu)
+        arr[q] = lll_instance(wl.N, wl.delta, L0.ctypes.data, wl.s, lam.ctypes.data, LLL_DRIVER_NIG,
+                              lll_nig(wl.alpha, wl.beta, wl.dbar, mu), len(x), x.ctypes.data, W.ctypes.data,
+                              st.shape[1], st.ctypes.data, int(wl.paths))
+    h = ctypes.c_void_p()
+    _check(lib.lll_batch_init(ctypes.byref(h), len(instances), arr, ctypes.c_void_p(stream or None)))
+    return h, keep
+
+
+def lll_batch_set_launch(b, threads=0, blocks_per_sm=0, chunk_rows=0):
+    _check(load().lll_batch_set_launch(b, int(threads), int(blocks_per_sm), int(chunk_rows)))
+
+
+def lll_batch_use_graph(b, enable=True):
+    _check(load().lll_batch_use_graph(b, 1 if enable else 0))
+
+
+def lll_batch_simulate(b, scheme, seed):
+    _check(load().lll_batch_simulate(b, int(scheme), int(seed)))
+
+
+def lll_batch_prices(b, q, n, ns):
+    p = np.zeros((n, ns))
+    se = np.zeros((n, ns))
+    _check(load().lll_batch_prices(b, int(q), _d(p), _d(se)))
+    return p, se
+
+
+def lll_batch_kernel_ms(b):
+    ms = ctypes.c_float()
+    _check(load().lll_batch_kernel_ms(b, ctypes.byref(ms)))
+    return ms.value
+
+
+def lll_batch_destroy(b):
+    if b:
+        load().lll_batch_destroy(b)
+
+
 def lll_last_error(ctx=None) -> str:
     msg = load().lll_last_error(ctx)
     return msg.decode() if msg else ""
@@ -296,8 +358,8 @@ class LevyLibor:
     def kernel_ms(self):
         return lll_kernel_ms(self.ctx)
 
-    def set_launch(self, threads=0, blocks_per_sm=0, chunk_rows=0, paths_per_thread=0):
-        lll_set_launch(self.ctx, threads, blocks_per_sm, chunk_rows, paths_per_thread)
+    def set_launch(self, threads=0, blocks_per_sm=0, chunk_rows=0, paths_per_thread=0, lanes_per_path=0):
+        lll_set_launch(self.ctx, threads, blocks_per_sm, chunk_rows, paths_per_thread, lanes_per_path)
 
     def close(self):
         if self.ctx:

@@ -1,0 +1,162 @@
+"""The learned compensator on the GPU (BF16 tensor-core kernels) against the
+FP64 oracle MLP, and the LLL_MLP scheme against the quadrature full scheme.
+
+Tolerances follow from BF16: weights, inputs and hidden activations are
+rounded to 8 significant bits (relative 2^-9), accumulation is FP32, so the
+network output and every gradient tensor must agree with the FP64 oracle
+evaluated on the same BF16-rounded weights and inputs to a few 1e-2 in
+relative norm.  The scheme must price caplets within 0.5 bp (5e-5) of the
+quadrature full scheme; the gain test compares it with the same scheme with
+the learned part removed (a zero network, i.e. the compensator at zero
+weights C_i only).
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from oracle import oracle as ora
+from oracle import quadrature
+from paper_1006_3340_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+H, L = 128, 3
+
+
+@pytest.fixture(scope="module")
+def lll():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    from paper_1006_3340_gb300 import lll as mod
+
+    mod.load()
+    return mod
+
+
+def bf16(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def _oracle_params(flat, offs, in_dim, in_pad):
+    params = []
+    for l in range(L):
+        din = in_pad if l == 0 else H
+        W = bf16(flat[offs[2 * l]: offs[2 * l] + H * din]).reshape(H, din).astype(np.float64)
+        if l == 0:
+            W = W[:, :in_dim]
+        params.append((W, flat[offs[2 * l + 1]: offs[2 * l + 1] + H].astype(np.float64)))
+    wout = bf16(flat[offs[2 * L]: offs[2 * L] + H]).astype(np.float64)[None, :]
+    params.append((wout, flat[offs[2 * L + 1]: offs[2 * L + 1] + 1].astype(np.float64)))
+    return params
+
+
+def _flat_grads(g, offs, in_dim, in_pad):
+    out = []
+    for l in range(L):
+        din = in_pad if l == 0 else H
+        W = g[offs[2 * l]: offs[2 * l] + H * din].reshape(H, din)
+        if l == 0:
+            assert np.all(W[:, in_dim:] == 0)
+            W = W[:, :in_dim]
+        out.append((W, g[offs[2 * l + 1]: offs[2 * l + 1] + H]))
+    out.append((g[offs[2 * L]: offs[2 * L] + H][None, :], g[offs[2 * L + 1]: offs[2 * L + 1] + 1]))
+    return out
+
+
+def test_forward_and_gradients_match_fp64_oracle(lll):
+    wl = workloads.large_single(paths=1024)
+    sim = lll.LevyLibor(wl)
+    try:
+        lll.lll_mlp_init(sim.ctx, H, L, seed=3)
+        n_params, in_dim, in_pad, offs = lll.lll_mlp_layout(sim.ctx, L)
+        flat, _ = lll.lll_mlp_params(sim.ctx, 0, count=n_params)
+        rng = np.random.default_rng(5)
+        rows = 1000
+        x = bf16(rng.normal(size=(rows, in_dim)))
+        y = rng.normal(size=rows).astype(np.float32)
+        out, g, loss = lll.lll_mlp_eval(sim.ctx, x, y, n_params, want_grads=True)
+    finally:
+        sim.close()
+    params = _oracle_params(flat, offs, in_dim, in_pad)
+    out_o, _ = omlp.forward(params, x.astype(np.float64))
+    loss_o, grads_o = omlp.loss_and_grads(params, x.astype(np.float64), y.astype(np.float64))
+    assert np.abs(out - out_o).max() <= 2e-2 * np.abs(out_o).max()
+    assert abs(loss - loss_o) <= 2e-2 * loss_o
+    for (gW, gb), (oW, ob) in zip(_flat_grads(g, offs, in_dim, in_pad), grads_o):
+        assert np.linalg.norm(gW - oW) <= 3e-2 * np.linalg.norm(oW)
+        assert np.linalg.norm(gb - ob) <= 3e-2 * np.linalg.norm(ob)
+
+
+def test_training_reduces_loss_and_roundtrips_through_file(lll):
+    wl = workloads.large_single(paths=4096)
+    sim = lll.LevyLibor(wl)
+    sim2 = lll.LevyLibor(wl)
+    try:
+        loss = lll.lll_mlp_train(sim.ctx, hidden=H, layers=L, train_paths=1 << 14, records_per_path=4,
+                                 epochs=3, batch=4096, lr=2e-3, lr_final=2e-4, seed=11)
+        assert loss < 0.1, loss  # targets are scaled to unit RMS
+        n_params, in_dim, _, _ = lll.lll_mlp_layout(sim.ctx, L)
+        x = bf16(np.random.default_rng(1).normal(size=(64, in_dim)) * 0.3)
+        a, _, _ = lll.lll_mlp_eval(sim.ctx, x)
+        with tempfile.TemporaryDirectory() as d:
+            path = os.path.join(d, "net.bin")
+            lll.lll_mlp_save(sim.ctx, path)
+            lll.lll_mlp_load(sim2.ctx, path)
+        b, _, _ = lll.lll_mlp_eval(sim2.ctx, x)
+        assert np.array_equal(a, b)
+    finally:
+        sim.close()
+        sim2.close()
+
+
+@pytest.fixture(scope="module")
+def trained(lll):
+    wl = workloads.large_single(paths=1 << 16)
+    x, W = quadrature.rule_for(wl)
+    sim = lll.LevyLibor(wl, x, W)
+    loss = lll.lll_mlp_train(sim.ctx, hidden=H, layers=L, train_paths=1 << 16, records_per_path=8,
+                             epochs=4, batch=8192, lr=2e-3, lr_final=1e-4, seed=7)
+    yield wl, x, W, sim, loss
+    sim.close()
+
+
+def _run(sim, scheme, count):
+    sim.simulate(scheme, snapshots=count)
+    p, se = sim.prices()
+    return p, se, sim.paths(0, count).astype(np.float64)
+
+
+def test_mlp_scheme_within_half_bp_of_quadrature_and_gains_over_no_network(lll, trained):
+    wl, x, W, sim, loss = trained
+    cnt = 4096
+    p_full, se_full, z_full = _run(sim, "full", cnt)
+    p_mlp, _, z_mlp = _run(sim, "mlp", cnt)
+    assert np.abs(p_mlp - p_full).max() <= 5e-5
+    n_params, _, _, _ = lll.lll_mlp_layout(sim.ctx, L)
+    flat, scales = lll.lll_mlp_params(sim.ctx, 0, count=n_params)
+    try:
+        lll.lll_mlp_params(sim.ctx, 1, np.zeros_like(flat), scales=scales)  # learned part removed
+        p_zero, _, z_zero = _run(sim, "mlp", cnt)
+    finally:
+        lll.lll_mlp_params(sim.ctx, 1, flat, scales=scales)
+    mask = ~np.isnan(z_full)
+    err_mlp = np.abs(z_mlp[mask] - z_full[mask]).max()
+    err_zero = np.abs(z_zero[mask] - z_full[mask]).max()
+    assert err_mlp < 0.2 * err_zero, (err_mlp, err_zero)
+    assert np.abs(p_mlp - p_full).max() <= np.abs(p_zero - p_full).max() + 1e-12
+
+
+def test_mlp_scheme_against_fp64_oracle(lll, trained):
+    wl, x, W, sim, loss = trained
+    cnt = 2048
+    sim.simulate("mlp", paths=cnt)
+    p_mlp, _ = sim.prices()
+    ref = ora.simulate(ora.OracleModel(wl, x, W), ora.FULL, npaths=cnt)
+    assert np.abs(p_mlp - ref["price"]).max() <= 5e-5  # 0.5 bp of notional

@@ -82,13 +82,16 @@ def test_long_dated_subset(lll, scheme):
 
 @pytest.mark.parametrize("N,s,Q,paths", [(2, 1, 8, 1), (3, 2, 8, 33), (5, 3, 20, 200), (7, 4, 40, 129)])
 @pytest.mark.parametrize("scheme", ["full", "picard", "frozen"])
-def test_tiny_edge_shapes(lll, N, s, Q, paths, scheme):
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_tiny_edge_shapes(lll, N, s, Q, paths, scheme, lanes):
     wl = workloads.tiny(N=N, s=s, Q=Q, paths=paths)
-    _compare(lll, wl, scheme, paths)
+    _compare(lll, wl, scheme, paths, launch=(0, 0, 0, 0, lanes if scheme != "frozen" else 1))
 
 
-@pytest.mark.parametrize("launch", [(32, 0, 1, 1), (64, 1, 2, 2), (256, 0, 3, 1), (96, 2, 0, 2),
-                                    (128, 0, 0, 1), (256, 0, 0, 2)])
+@pytest.mark.parametrize("launch", [(32, 0, 1, 1, 1), (64, 1, 2, 2, 1), (256, 0, 3, 1, 1), (96, 2, 0, 2, 1),
+                                    (128, 0, 0, 1, 1), (256, 0, 0, 2, 1), (32, 0, 1, 0, 4), (64, 1, 2, 0, 4),
+                                    (256, 0, 3, 0, 4), (96, 2, 0, 0, 4), (128, 0, 0, 0, 4), (64, 0, 3, 0, 2),
+                                    (128, 0, 0, 0, 2)])
 def test_launch_shapes_agree(lll, launch):
     wl = workloads.large_single()
     _compare(lll, wl, "picard", 300, launch=launch)
