@@ -284,6 +284,13 @@ def main():
         pp, _ = sims["picard"].prices()
         pf, _ = sims["full"].prices()
         per["picard_vs_full_max_bp"] = float(np.abs(pp - pf).max() * 1e4)
+    if world > 1 and "picard" in sims:
+        # one gather of the FP64 payoff sums, added in rank order (outside the timing)
+        from paper_1006_3340_gb300 import shard
+        s1, s2, cnt = sims["picard"].sums()
+        m1, m2, mcnt = shard.merge_sums(s1, s2, cnt)
+        per["picard_merged_paths"] = mcnt
+        per["picard_merged_atm_T10y"] = float(m1[n - 1, ns // 2] / mcnt)
     if "mlp" in per and "full" in per:
         pm, _ = sims["mlp"].prices()
         pf, _ = sims["full"].prices()

@@ -74,8 +74,8 @@ void free_all(lll_ctx *c)
 int default_chunk_rows(int n, int QP)
 {
     if (QP == 0) return std::min(n, 64);
-    // Keep the double-buffered node tables near 48 KB.
-    const int rows = (48 * 1024) / (2 * (QP / 2) * (int)sizeof(float4));
+    // Keep the double-buffered node tables near 24 KB (room for five blocks per SM).
+    const int rows = (24 * 1024) / (2 * (QP / 2) * (int)sizeof(float4));
     return std::max(1, std::min(n, rows));
 }
 
@@ -124,7 +124,7 @@ int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, u
         e = (cudaError_t)group_kernel_prepare(scheme, QPk, lpp, smem, T, &occ);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "group kernel attributes");
     } else {
-        e = (cudaError_t)path_kernel_prepare(scheme, QPk, R, smem);
+        e = (cudaError_t)path_kernel_prepare(scheme, QPk, R, T, smem);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaFuncSetAttribute");
         e = (cudaError_t)path_kernel_occupancy(scheme, QPk, R, T, smem, &occ);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "occupancy");

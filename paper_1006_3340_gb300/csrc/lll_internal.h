@@ -67,7 +67,7 @@ struct LaunchPlan {
 int launch_path_kernel(int scheme, int QP, int R, int grid, int threads, size_t smem, cudaStream_t st,
                        const PathArgs &a);
 int path_kernel_occupancy(int scheme, int QP, int R, int threads, size_t smem, int *blocks_per_sm);
-int path_kernel_prepare(int scheme, int QP, int R, size_t smem);
+int path_kernel_prepare(int scheme, int QP, int R, int threads, size_t smem);
 bool path_kernel_supported(int scheme, int QP, int R);
 size_t path_kernel_smem(int QP, int n, int ns, int threads, int chunk_rows);
 

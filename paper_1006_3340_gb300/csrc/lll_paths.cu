@@ -321,8 +321,18 @@ __device__ __forceinline__ void run_tile(const PathArgs &a, const Smem &sm, floa
     }
 }
 
-template <int SCHEME, int QP, int R>
-__global__ void __launch_bounds__(kMaxThreads) path_kernel(const PathArgs a)
+// Register budget classes (resident warps hide shared-memory latency):
+//   LB 0: up to 255 registers (node tables of 96 or 128 nodes),
+//   LB 1: 128 registers, two 256-thread or four 128-thread blocks per SM,
+//   LB 2: 102 registers, five blocks of at most 128 threads per SM.
+template <int LB>
+struct Bounds {
+    static constexpr int threads = LB == 2 ? 128 : kMaxThreads;
+    static constexpr int blocks = LB == 0 ? 1 : (LB == 1 ? 2 : 5);
+};
+
+template <int SCHEME, int QP, int R, int LB>
+__global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks) path_kernel(const PathArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NST = (SCHEME == PICARD) ? 2 : 1;
@@ -394,36 +404,44 @@ typedef void (*KernelFn)(const PathArgs);
 // Paths per thread: 2 shares every staged table load between two paths
 // (halving shared-memory traffic per unit); compiled where the registers of
 // two node arrays fit (padded Q <= 64).
+// Budget by node count: <= 32 nodes and <= 128 threads: LB 2; <= 96 nodes:
+// LB 1; more: LB 0.  Two paths per thread keep the full budget.
 template <int SCHEME, int QP>
-KernelFn pick_r(int R)
+KernelFn pick_r(int R, int T)
 {
-    if (R == 1) return path_kernel<SCHEME, QP, 1>;
+    if (R == 1) {
+        if constexpr (QP <= 32) {
+            if (T <= 128) return path_kernel<SCHEME, QP, 1, 2>;
+        }
+        if constexpr (QP <= 96) return path_kernel<SCHEME, QP, 1, 1>;
+        else return path_kernel<SCHEME, QP, 1, 0>;
+    }
     if constexpr (QP <= 64) {
-        if (R == 2) return path_kernel<SCHEME, QP, 2>;
+        if (R == 2) return path_kernel<SCHEME, QP, 2, 0>;
     }
     return nullptr;
 }
 
 template <int SCHEME>
-KernelFn pick_qp(int QP, int R)
+KernelFn pick_qp(int QP, int R, int T)
 {
     switch (QP) {
-    case 0: return pick_r<SCHEME, 0>(R);
-    case 16: return pick_r<SCHEME, 16>(R);
-    case 32: return pick_r<SCHEME, 32>(R);
-    case 64: return pick_r<SCHEME, 64>(R);
-    case 96: return pick_r<SCHEME, 96>(R);
-    case 128: return pick_r<SCHEME, 128>(R);
+    case 0: return pick_r<SCHEME, 0>(R, T);
+    case 16: return pick_r<SCHEME, 16>(R, T);
+    case 32: return pick_r<SCHEME, 32>(R, T);
+    case 64: return pick_r<SCHEME, 64>(R, T);
+    case 96: return pick_r<SCHEME, 96>(R, T);
+    case 128: return pick_r<SCHEME, 128>(R, T);
     default: return nullptr;
     }
 }
 
-KernelFn pick(int scheme, int QP, int R)
+KernelFn pick(int scheme, int QP, int R, int T)
 {
     switch (scheme) {
-    case FULL: return pick_qp<FULL>(QP, R);
-    case PICARD: return pick_qp<PICARD>(QP, R);
-    case FROZEN: return pick_r<FROZEN, 0>(R);
+    case FULL: return pick_qp<FULL>(QP, R, T);
+    case PICARD: return pick_qp<PICARD>(QP, R, T);
+    case FROZEN: return pick_r<FROZEN, 0>(R, T);
     default: return nullptr;
     }
 }
@@ -477,23 +495,23 @@ int launch_batch_kernel(int scheme, int QP, int grid, int threads, size_t smem, 
     return (int)cudaGetLastError();
 }
 
-bool path_kernel_supported(int scheme, int QP, int R) { return pick(scheme, QP, R) != nullptr; }
+bool path_kernel_supported(int scheme, int QP, int R) { return pick(scheme, QP, R, kMaxThreads) != nullptr; }
 
 size_t path_kernel_smem(int QP, int n, int ns, int threads, int chunk_rows)
 {
     return smem_bytes(QP, n, ns, threads, chunk_rows);
 }
 
-int path_kernel_prepare(int scheme, int QP, int R, size_t smem)
+int path_kernel_prepare(int scheme, int QP, int R, int threads, size_t smem)
 {
-    KernelFn f = pick(scheme, QP, R);
+    KernelFn f = pick(scheme, QP, R, threads);
     if (!f) return (int)cudaErrorInvalidValue;
     return (int)cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
 int path_kernel_occupancy(int scheme, int QP, int R, int threads, size_t smem, int *blocks_per_sm)
 {
-    KernelFn f = pick(scheme, QP, R);
+    KernelFn f = pick(scheme, QP, R, threads);
     if (!f) return (int)cudaErrorInvalidValue;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, smem);
 }
@@ -501,7 +519,7 @@ int path_kernel_occupancy(int scheme, int QP, int R, int threads, size_t smem, i
 int launch_path_kernel(int scheme, int QP, int R, int grid, int threads, size_t smem, cudaStream_t st,
                        const PathArgs &a)
 {
-    KernelFn f = pick(scheme, QP, R);
+    KernelFn f = pick(scheme, QP, R, threads);
     if (!f) return (int)cudaErrorInvalidValue;
     // The frozen kernel stages no node table; its QP argument is ignored.
     f<<<grid, threads, smem, st>>>(a);
