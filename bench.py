@@ -96,6 +96,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def _traffic(key):
+    """DRAM bytes per launch from profiles/traffic.json, if the kernel's sources
+    are unchanged since the counters were taken (else None)."""
+    import hashlib
+    try:
+        entry = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[key]
+        csrc = os.path.join(ROOT, "paper_1006_3340_gb300", "csrc")
+        for fn, digest in entry["sources"].items():
+            if hashlib.sha1(open(os.path.join(csrc, fn), "rb").read()).hexdigest() != digest:
+                return None
+        return entry["dram_bytes_read"] + entry["dram_bytes_write"]
+    except Exception:
+        return None
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -183,6 +198,9 @@ def main():
     ap.add_argument("--schemes", default="picard,full,mlp")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="library default launch shapes")
+    ap.add_argument("--launch", default="", help="fixed launch shape for the quadrature schemes: "
+                    "threads,blocks_per_sm,chunk_rows,paths_per_thread,lanes_per_path (no tuning)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -233,6 +251,22 @@ def main():
             lll.lll_simulate(sims[s].ctx, lll.SCHEMES[s], first, wl.paths, wl.seed)
             if evs is not None:
                 evs[i][1].record()
+
+    # launch shapes of the quadrature schemes by the project's autotuner
+    from paper_1006_3340_gb300 import autotune
+    tuned = {}
+    if args.launch:
+        shape = [int(v) for v in args.launch.split(",")]
+        for s in schemes:
+            if s in ("picard", "full", "frozen"):
+                sims[s].set_launch(*shape)
+                tuned[s] = {"launch(threads,bps,chunk,ppt,lanes)": shape, "ms": None}
+    elif not args.no_tune:
+        cands = [(128, 0, 0, 1, 1), (256, 0, 0, 1, 1), (128, 0, 0, 1, 2), (256, 0, 0, 1, 2)]
+        for s in schemes:
+            if s in ("picard", "full", "frozen"):
+                r = autotune.tune(sims[s], s, candidates=cands, repeats=2, use_cache=False)
+                tuned[s] = {"launch(threads,bps,chunk,ppt,lanes)": r["launch"], "ms": r["ms"]}
 
     for _ in range(args.warmup):
         one_step()
@@ -309,8 +343,11 @@ def main():
     def quad_roofline(s):
         ms = statistics.mean(per_scheme_ms[s])
         ach = units * 3 * wl.Q / (ms * 1e-3) / 1e12
+        shape = tuned.get(s, {}).get("launch(threads,bps,chunk,ppt,lanes)")
+        lanes = shape[4] if shape and shape[4] else 1
+        traffic = _traffic(f"{s}/QP{wl.Q}/lanes{lanes}") if wl.paths == 1 << 20 else None
         r = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFP32-lane-op/s",
-             "frac": ach / fp32_peak, "traffic": None, "kernel": f"{s} path kernel, QP={wl.Q}",
+             "frac": ach / fp32_peak, "traffic": traffic, "kernel": f"{s} path kernel, QP={wl.Q}",
              "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS)"}
         if clocks and clocks.get("sm_mhz"):
             r["frac_at_sampled_clock"] = ach / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
@@ -323,7 +360,8 @@ def main():
         ach = units * 2 * macs / (ms * 1e-3) / 1e12
         peak = float(peaks.get("bf16_tflops_sustained", 1679.9))
         return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": None, "kernel": "mlp path kernel (mma.sync bf16)",
+                "traffic": _traffic("mlp/L3/KT3") if wl.paths == 1 << 20 else None,
+                "kernel": "mlp path kernel (mma.sync bf16)",
                 "peak_basis": "bf16_tflops_sustained of MEASURED_PEAKS"}
 
     dom = max(schemes, key=lambda s: statistics.mean(per_scheme_ms[s]))
@@ -343,6 +381,8 @@ def main():
             t0 = time.perf_counter()
             for s in schemes:
                 sim = lll.LevyLibor(wl, x, W, stream=stream)
+                if s in tuned:
+                    sim.set_launch(*tuned[s]["launch(threads,bps,chunk,ppt,lanes)"])
                 if s == "mlp":
                     lll.lll_mlp_init(sim.ctx, 128, 3, 0)
                     lll.lll_mlp_params(sim.ctx, 1, mlp_params[0], scales=mlp_params[1])
@@ -374,7 +414,7 @@ def main():
                            f"({L2_FLUSH_BYTES >> 20} MiB write outside the events)"},
                 "per_scheme": per, "roofline": roofline,
                 "roofline_picard": quad_roofline("picard") if "picard" in schemes else None,
-                "mlp": mlp_info, "cpu_baseline": cpu, "e2e": e2e,
+                "mlp": mlp_info, "autotuned": tuned, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": 2 * len(schemes) * args.steps}
         print(json.dumps(line), flush=True)
     for s in sims.values():

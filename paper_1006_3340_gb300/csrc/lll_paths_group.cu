@@ -54,6 +54,24 @@ __device__ __forceinline__ double warp_sum(double v)
 
 __host__ __device__ inline size_t a16(size_t v) { return (v + 15) & ~size_t(15); }
 
+// The weights of the G paths of this lane's group, from each lane's own.
+template <int G>
+__device__ __forceinline__ void group_weights(float wown, int t, int gbase, float2 (&w2)[G])
+{
+    if constexpr (G == 2) {
+        const float other = __shfl_xor_sync(0xffffffffu, wown, 1);
+        const float w0 = t ? other : wown, w1 = t ? wown : other;
+        w2[0] = make_float2(w0, w0);
+        w2[1] = make_float2(w1, w1);
+    } else {
+#pragma unroll
+        for (int q = 0; q < G; ++q) {
+            const float wq = __shfl_sync(0xffffffffu, wown, gbase + q);
+            w2[q] = make_float2(wq, wq);
+        }
+    }
+}
+
 __host__ __device__ inline size_t group_smem_bytes(int QP, int n, int ns, int threads, int CH)
 {
     size_t b = 0;
@@ -159,14 +177,8 @@ __global__ void __launch_bounds__(kMaxThreads, (QP <= 64 ? 2 : 1)) group_kernel(
                 float v0n = st[(size_t)(itop - 1) * T];
                 float v1n = (NST == 2) ? st[(size_t)(n + itop - 1) * T] : 0.0f;
                 float2 wn2[G];
-                {
-                    const float wo = weight_of(sc0[itop - 1] + (SCHEME == PICARD ? rb[itop - ibot].z : 0.0f) + v0n);
-#pragma unroll
-                    for (int q = 0; q < G; ++q) {
-                        const float wq = __shfl_sync(0xffffffffu, wo, gbase + q);
-                        wn2[q] = make_float2(wq, wq);
-                    }
-                }
+                group_weights<G>(weight_of(sc0[itop - 1] + (SCHEME == PICARD ? rb[itop - ibot].z : 0.0f) + v0n),
+                                 t, gbase, wn2);
                 for (int i = itop; i >= ibot; --i) {
                     const int r = i - ibot;
                     const float4 rc = rb[r]; // lambda, K, D0, b0*h
@@ -177,12 +189,8 @@ __global__ void __launch_bounds__(kMaxThreads, (QP <= 64 ? 2 : 1)) group_kernel(
                     if (i > ibot) {
                         v0n = st[(size_t)(i - 2) * T];
                         if (NST == 2) v1n = st[(size_t)(n + i - 2) * T];
-                        const float wo = weight_of(sc0[i - 2] + (SCHEME == PICARD ? rb[r - 1].z : 0.0f) + v0n);
-#pragma unroll
-                        for (int q = 0; q < G; ++q) {
-                            const float wq = __shfl_sync(0xffffffffu, wo, gbase + q);
-                            wn2[q] = make_float2(wq, wq);
-                        }
+                        group_weights<G>(weight_of(sc0[i - 2] + (SCHEME == PICARD ? rb[r - 1].z : 0.0f) + v0n),
+                                         t, gbase, wn2);
                     }
                     float2 acc[G][2];
                     const float4 *tr = tb + (size_t)r * Q2 + t;
@@ -205,8 +213,8 @@ __global__ void __launch_bounds__(kMaxThreads, (QP <= 64 ? 2 : 1)) group_kernel(
                     }
                     // reduce-scatter over the G lanes: lane t ends with the total of path t
                     if constexpr (G == 2) {
-                        const float rx = __shfl_xor_sync(0xffffffffu, part[t ^ 1], 1);
-                        part[0] = part[t] + rx;
+                        const float keep = t ? part[1] : part[0], send = t ? part[0] : part[1];
+                        part[0] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
                     } else {
                         const bool hi = (t & 2) != 0;
                         const float s0 = hi ? part[0] : part[2], s1 = hi ? part[1] : part[3];
