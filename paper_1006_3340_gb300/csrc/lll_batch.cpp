@@ -93,7 +93,7 @@ int build_schedule(lll_batch *b, int scheme)
     if (b->scheme == scheme) return LLL_OK;
     free_schedule(b);
     const int T = b->threads;
-    const int CH = b->chunk_rows > 0 ? b->chunk_rows : std::min(b->n_max, std::max(1, (48 * 1024) / (2 * (b->QP / 2) * 16)));
+    const int CH = b->chunk_rows > 0 ? b->chunk_rows : std::min(b->n_max, std::max(1, (48 * 1024) / (2 * (b->QP / 4) * 16)));
     const int nst = scheme == LLL_PICARD ? 2 : 1;
     // smem as for the path kernel, sized for the largest instance
     size_t smem = path_kernel_smem(b->QP, b->n_max, b->ns_max, T, CH);

@@ -64,7 +64,7 @@ void free_all(lll_ctx *c)
     cudaFree(c->d_lam); cudaFree(c->d_x); cudaFree(c->d_W); cudaFree(c->d_w0); cudaFree(c->d_b0);
     cudaFree(c->d_tab); cudaFree(c->d_row); cudaFree(c->d_Z0); cudaFree(c->d_c0);
     cudaFree(c->d_strikes); cudaFree(c->d_partials); cudaFree(c->d_sums); cudaFree(c->d_state);
-    cudaFree(c->d_snap); cudaFree(c->d_C);
+    cudaFree(c->d_snap); cudaFree(c->d_C); cudaFree(c->d_cn);
     mlp_free(c->mlp);
     c->mlp = nullptr;
     for (auto &e : c->ev)
@@ -75,7 +75,7 @@ int default_chunk_rows(int n, int QP)
 {
     if (QP == 0) return std::min(n, 64);
     // Keep the double-buffered node tables near 24 KB (room for five blocks per SM).
-    const int rows = (24 * 1024) / (2 * (QP / 2) * (int)sizeof(float4));
+    const int rows = (24 * 1024) / (2 * (QP / 4) * (int)sizeof(float4));
     return std::max(1, std::min(n, rows));
 }
 
@@ -135,7 +135,7 @@ int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, u
     const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)bps * ctx->sm_count);
     const int nst = (scheme == LLL_PICARD) ? 2 : 1;
     PathArgs a{};
-    a.tab = ctx->d_tab; a.row = ctx->d_row; a.Z0 = ctx->d_Z0; a.c0 = ctx->d_c0;
+    a.tab = ctx->d_tab; a.cn = ctx->d_cn; a.row = ctx->d_row; a.Z0 = ctx->d_Z0; a.c0 = ctx->d_c0;
     a.strikes = ctx->d_strikes; a.partials = nullptr; a.state = nullptr;
     a.snap = nullptr; a.n_snap = 0; a.snap_stride = 1; a.snap_pitch = 0;
     a.first_path = first_path; a.paths = paths;
@@ -258,7 +258,8 @@ int lll_init(lll_ctx **out, int N, double tenor_delta, const double *L0, int ste
     bool ok = dalloc(&c->d_lam, rows) == cudaSuccess && dalloc(&c->d_x, std::max(Q, 1)) == cudaSuccess &&
               dalloc(&c->d_W, std::max(Q, 1)) == cudaSuccess && dalloc(&c->d_w0, n) == cudaSuccess &&
               dalloc(&c->d_b0, rows) == cudaSuccess &&
-              dalloc(&c->d_tab, rows * std::max(QP / 2, 1)) == cudaSuccess &&
+              dalloc(&c->d_tab, rows * std::max(QP / 4, 1)) == cudaSuccess &&
+              dalloc(&c->d_cn, std::max(QP, 4)) == cudaSuccess &&
               dalloc(&c->d_row, rows) == cudaSuccess && dalloc(&c->d_C, rows) == cudaSuccess &&
               dalloc(&c->d_Z0, n) == cudaSuccess &&
               dalloc(&c->d_c0, n) == cudaSuccess;
@@ -280,7 +281,7 @@ int lll_init(lll_ctx **out, int N, double tenor_delta, const double *L0, int ste
     INIT_TRY(cudaMemcpyAsync(c->d_Z0, Z0.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
     INIT_TRY(cudaMemcpyAsync(c->d_c0, c0.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st));
     INIT_TRY(cudaMemsetAsync(c->d_row, 0, sizeof(float4) * rows, st));
-    INIT_TRY((cudaError_t)launch_tables(c->d_lam, c->d_x, c->d_W, n, S, Q, QP, c->d_tab, c->d_row, c->d_C, st));
+    INIT_TRY((cudaError_t)launch_tables(c->d_lam, c->d_x, c->d_W, n, S, Q, QP, c->d_tab, c->d_cn, c->d_row, c->d_C, st));
     INIT_TRY((cudaError_t)launch_frozen_drift(c->d_lam, c->d_x, c->d_W, c->d_w0, n, S, Q, c->c, c->h,
                                               c->d_b0, c->d_row, st));
     // The host vectors above go out of scope: wait for the copies.

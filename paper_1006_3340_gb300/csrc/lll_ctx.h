@@ -24,6 +24,7 @@ struct lll_ctx {
     // device
     double *d_lam = nullptr, *d_x = nullptr, *d_W = nullptr, *d_w0 = nullptr, *d_b0 = nullptr;
     float4 *d_tab = nullptr, *d_row = nullptr;
+    float *d_cn = nullptr; // [QP]: c_j = W_j / x_j^2
     float *d_C = nullptr; // [S][n]: C_l(t_k), the compensator at zero weights (FP64-built)
     float *d_Z0 = nullptr, *d_c0 = nullptr, *d_strikes = nullptr;
     double *d_partials = nullptr, *d_sums = nullptr;

@@ -17,7 +17,8 @@ constexpr int kMaxThreads = 256;
 
 // Arguments of the path kernels (one simulation of one scheme).
 struct PathArgs {
-    const float4 *tab;    // [S][n][QP/2]: (E_j, E_j+1, a_j, a_j+1), E = e^{lambda x_j}-1, a = W_j E / x_j^2
+    const float4 *tab;    // [S][n][QP/4]: (E_j .. E_j+3), E_lj = e^{lambda_l(t_k) x_j} - 1
+    const float *cn;      // [QP]: c_j = W_j / x_j^2 (0 on padding nodes)
     const float4 *row;    // [S][n]: (lambda_l(t_k), K_l(k), D0_l(t_k), b0_l(t_k) * h)
     const float *Z0;      // [n]: log L(0, T_l)
     const float *c0;      // [n]: log L(0, T_l) + log delta
@@ -86,7 +87,7 @@ int launch_batch_kernel(int scheme, int QP, int grid, int threads, size_t smem, 
 
 // Launchers implemented in lll_tables.cu.
 int launch_tables(const double *lam, const double *x, const double *W, int n, int S, int Q, int QP,
-                  float4 *tab, float4 *row, float *Ctab, cudaStream_t st);
+                  float4 *tab, float *cn, float4 *row, float *Ctab, cudaStream_t st);
 int launch_frozen_drift(const double *lam, const double *x, const double *W, const double *w0,
                         int n, int S, int Q, double c, double h, double *b0, float4 *row,
                         cudaStream_t st);

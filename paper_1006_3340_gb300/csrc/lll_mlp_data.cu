@@ -4,10 +4,10 @@
 // compensator, same tables as the path kernels) simulated on its own paths,
 // one thread per path.  At a few Euler steps per path, chosen by Philox, it
 // records the log-rate offsets log L_m(t_k) - log L_m(0) of all rates and,
-// for every live rate i, the target A_i - C_i = sum_j a_ij (P_j - 1): the
-// part of the compensator that depends on the later rates.  P_j - 1 is
-// carried directly, (P-1)' = (P-1) + w E (1 + (P-1)), so the small target
-// keeps its relative accuracy in FP32.
+// for every live rate i, the target A_i - C_i = sum_j E_ij c_j (P_j - 1): the
+// part of the compensator that depends on the later rates.  M_j = c_j (P_j - 1)
+// is carried directly, M' = M + w E (c_j + M), so the small target keeps its
+// relative accuracy in FP32.
 // gather_kernel: a training batch of feature rows and scaled targets, drawn
 // uniformly over records and, within a record, over its live rates.
 #include <cuda_bf16.h>
@@ -24,7 +24,7 @@ template <int QP>
 __global__ void datagen_kernel(const PathArgs a, const float *Ctab, int R, uint32_t rec_key,
                                float *state, float *rec_u, float *rec_y, int *rec_k)
 {
-    constexpr int Q2 = QP / 2;
+    constexpr int Q4 = QP / 4;
     const uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= a.paths) return;
     const int n = a.n, s = a.s, S = a.S, N = n + 1;
@@ -52,24 +52,28 @@ __global__ void datagen_kernel(const PathArgs a, const float *Ctab, int R, uint3
             for (int m = 1; m < imin; ++m) y[m - 1] = 0.0f;
             rec_k[slot[q]] = k;
         }
-        float2 Pm[Q2];
+        float4 M[Q4];
 #pragma unroll
-        for (int j = 0; j < Q2; ++j) Pm[j] = make_float2(0.0f, 0.0f);
+        for (int j = 0; j < Q4; ++j) M[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         for (int i = n; i >= imin; --i) {
             const size_t row = (size_t)k * n + (i - 1);
             const float4 rc = __ldg(&a.row[row]);
             const float zoff = st[(size_t)(i - 1) * pitch];
             const float w = 1.0f / (1.0f + expf(-(a.c0[i - 1] + zoff)));
             float dep = 0.0f;
-            const float4 *tr = a.tab + row * Q2;
+            const float4 *tr = a.tab + row * Q4;
+            const float4 *cq = reinterpret_cast<const float4 *>(a.cn);
 #pragma unroll
-            for (int j = 0; j < Q2; ++j) {
-                const float4 v = __ldg(&tr[j]);
-                dep = fmaf(v.z, Pm[j].x, dep);
-                dep = fmaf(v.w, Pm[j].y, dep);
-                const float t0 = w * v.x, t1 = w * v.y;
-                Pm[j].x = fmaf(t0, Pm[j].x, Pm[j].x + t0);
-                Pm[j].y = fmaf(t1, Pm[j].y, Pm[j].y + t1);
+            for (int j = 0; j < Q4; ++j) {
+                const float4 v = __ldg(&tr[j]), c = __ldg(&cq[j]);
+                dep = fmaf(v.x, M[j].x, dep);
+                dep = fmaf(v.y, M[j].y, dep);
+                dep = fmaf(v.z, M[j].z, dep);
+                dep = fmaf(v.w, M[j].w, dep);
+                M[j].x = fmaf(w * v.x, c.x + M[j].x, M[j].x);
+                M[j].y = fmaf(w * v.y, c.y + M[j].y, M[j].y);
+                M[j].z = fmaf(w * v.z, c.z + M[j].z, M[j].z);
+                M[j].w = fmaf(w * v.w, c.w + M[j].w, M[j].w);
             }
             for (int q = 0; q < nrec; ++q) rec_y[(size_t)slot[q] * n + (i - 1)] = dep;
             const float A = Ctab[row] + dep;

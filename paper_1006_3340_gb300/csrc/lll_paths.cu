@@ -8,11 +8,13 @@
 // of the beta factors of Eq. (Levy-LIBOR-beta).  The jump part of the drift of
 // Eq. (LIBOR-drift-PT) is then
 //     A_i = int [(e^{lambda_i x}-1) prod_{l>i} beta_l - lambda_i x] F(dx)
-//         = K_i + sum_j a_ij P_j,
-// with a_ij = W_j (e^{lambda_i x_j}-1) / x_j^2 and K_i = C_i - sum_j a_ij,
-// C_i = sum_j W_j (e^{lambda_i x_j} - 1 - lambda_i x_j) / x_j^2 (both from FP64
-// tables).  The sweep costs 3 FP32 operations per (node, live rate): one FMA
-// into A_i, one multiply w_i E_ij and one FMA into P_j (packed as f32x2).
+//         = K_i + sum_j E_ij (c_j P_j),
+// with E_ij = e^{lambda_i x_j} - 1, c_j = W_j / x_j^2 and
+// K_i = C_i - sum_j c_j E_ij, C_i = sum_j c_j (E_ij - lambda_i x_j) (FP64
+// tables).  The sweep carries the scaled products P~_j = c_j P_j (P~_j = c_j
+// at the first rate of a step), so a table row holds E_ij alone, and costs 3
+// FP32 operations per (node, live rate), packed as f32x2:
+//     u = E_ij P~_j,   A_i += u,   P~_j += w_i u.
 //
 //  * FULL   (Eq. (LIBOR-drift-PT)): w_l from the simulated Z_l(t_k).
 //  * PICARD (Eq. (bdrift)):         w_l from Z^(1)_l(t_k) = Z_l(0) + D0_l(t_k)
@@ -77,8 +79,9 @@ __device__ __forceinline__ double warp_sum(double v)
 }
 
 struct Smem {
-    float4 *tab;  // [2][CH * QP/2]
+    float4 *tab;  // [2][CH * QP/4]
     float4 *row;  // [2][CH]
+    float2 *cn;   // [QP/2] c_j = W_j / x_j^2
     float *c0;    // [n]
     double *bsum; // [n * ns][4]: sum, comp, sumsq, comp
     double *red;  // [warps][ns][2]
@@ -89,8 +92,9 @@ __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(
 __host__ __device__ inline size_t smem_bytes(int QP, int n, int ns, int threads, int CH)
 {
     size_t b = 0;
-    b += align16(sizeof(float4) * 2 * (size_t)CH * (QP / 2));
+    b += align16(sizeof(float4) * 2 * (size_t)CH * (QP / 4));
     b += align16(sizeof(float4) * 2 * (size_t)CH);
+    b += align16(sizeof(float) * (size_t)QP);
     b += align16(sizeof(float) * (size_t)n);
     b += align16(sizeof(double) * 4 * (size_t)n * ns);
     b += align16(sizeof(double) * 2 * (size_t)(threads / 32) * ns);
@@ -102,9 +106,11 @@ __device__ inline Smem carve(unsigned char *base, int QP, int n, int ns, int thr
     Smem s;
     size_t o = 0;
     s.tab = reinterpret_cast<float4 *>(base + o);
-    o += align16(sizeof(float4) * 2 * (size_t)CH * (QP / 2));
+    o += align16(sizeof(float4) * 2 * (size_t)CH * (QP / 4));
     s.row = reinterpret_cast<float4 *>(base + o);
     o += align16(sizeof(float4) * 2 * (size_t)CH);
+    s.cn = reinterpret_cast<float2 *>(base + o);
+    o += align16(sizeof(float) * (size_t)QP);
     s.c0 = reinterpret_cast<float *>(base + o);
     o += align16(sizeof(float) * (size_t)n);
     s.bsum = reinterpret_cast<double *>(base + o);
@@ -124,10 +130,10 @@ __device__ __forceinline__ void issue_chunk(const PathArgs &a, const Smem &sm, i
     const int cnt = itop - ibot + 1;
     const size_t r0 = (size_t)k * n + (ibot - 1);
     if (QP > 0) {
-        constexpr int Q2 = QP / 2;
-        const float4 *src = a.tab + r0 * Q2;
-        float4 *dst = sm.tab + (size_t)b * CH * Q2;
-        for (int e = threadIdx.x; e < cnt * Q2; e += blockDim.x) cp_async16(dst + e, src + e);
+        constexpr int Q4 = QP / 4;
+        const float4 *src = a.tab + r0 * Q4;
+        float4 *dst = sm.tab + (size_t)b * CH * Q4;
+        for (int e = threadIdx.x; e < cnt * Q4; e += blockDim.x) cp_async16(dst + e, src + e);
     }
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) cp_async16(sm.row + b * CH + e, a.row + r0 + e);
 }
@@ -137,7 +143,8 @@ __device__ __forceinline__ void issue_chunk(const PathArgs &a, const Smem &sm, i
 template <int SCHEME, int QP, int R>
 __device__ __forceinline__ void run_tile(const PathArgs &a, const Smem &sm, float *st, uint64_t tile)
 {
-    constexpr int Q2 = QP > 0 ? QP / 2 : 1;
+    constexpr int Q2 = QP > 0 ? QP / 2 : 1; // node pairs
+    constexpr int Q4 = QP > 0 ? QP / 4 : 1; // table float4 entries per row
     constexpr int NST = (SCHEME == PICARD) ? 2 : 1;
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = a.n, s = a.s, S = a.S, ns = a.ns, CH = a.chunk_rows;
@@ -172,11 +179,16 @@ __device__ __forceinline__ void run_tile(const PathArgs &a, const Smem &sm, floa
 #pragma unroll
             for (int q = 0; q < R; ++q) dH[q] = draw_increment(a, p[q], (uint32_t)k);
 
+            // scaled products P~_j = c_j P_j, P = 1 above the top rate
             float2 P[R][Q2];
+            if (QP > 0) {
 #pragma unroll
-            for (int q = 0; q < R; ++q)
+                for (int j = 0; j < Q2; ++j) {
+                    const float2 cj = sm.cn[j];
 #pragma unroll
-                for (int j = 0; j < Q2; ++j) P[q][j] = make_float2(1.0f, 1.0f);
+                    for (int q = 0; q < R; ++q) P[q][j] = cj;
+                }
+            }
             float scont[R], num[R], Lm[R];
 #pragma unroll
             for (int q = 0; q < R; ++q) { scont[q] = 0.0f; num[q] = 1.0f; Lm[q] = 0.0f; }
@@ -191,7 +203,7 @@ __device__ __forceinline__ void run_tile(const PathArgs &a, const Smem &sm, floa
 
                 const int itop = n - c * CH;
                 const int ibot = max(imin, itop - CH + 1);
-                const float4 *tb = sm.tab + (size_t)buf * CH * Q2;
+                const float4 *tb = sm.tab + (size_t)buf * CH * Q4;
                 const float4 *rb = sm.row + buf * CH;
                 // state of the first row; each row prefetches the next one's
                 // State and weight of the first row; every row then loads the
@@ -229,20 +241,24 @@ __device__ __forceinline__ void run_tile(const PathArgs &a, const Smem &sm, floa
 #pragma unroll
                         for (int q = 0; q < R; ++q) bh[q] = rc.w;
                     } else if (QP > 0) {
-                        const float4 *tr = tb + (size_t)r * Q2;
+                        const float4 *tr = tb + (size_t)r * Q4;
                         float2 acc[R][4];
                         float2 w2[R];
 #pragma unroll
                         for (int q = 0; q < R; ++q) w2[q] = make_float2(w[q], w[q]);
 #pragma unroll
-                        for (int j = 0; j < Q2; ++j) {
-                            const float4 v = tr[j];
-                            const float2 e2 = make_float2(v.x, v.y);
-                            const float2 a2 = make_float2(v.z, v.w);
+                        for (int j4 = 0; j4 < Q4; ++j4) {
+                            const float4 v = tr[j4];
 #pragma unroll
-                            for (int q = 0; q < R; ++q) {
-                                acc[q][j & 3] = (j < 4) ? __fmul2_rn(a2, P[q][j]) : __ffma2_rn(a2, P[q][j], acc[q][j & 3]);
-                                P[q][j] = __ffma2_rn(__fmul2_rn(w2[q], e2), P[q][j], P[q][j]);
+                            for (int hf = 0; hf < 2; ++hf) {
+                                const int j = 2 * j4 + hf;
+                                const float2 e2 = hf ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+#pragma unroll
+                                for (int q = 0; q < R; ++q) {
+                                    const float2 u = __fmul2_rn(e2, P[q][j]);
+                                    acc[q][j & 3] = (j < 4) ? u : __fadd2_rn(acc[q][j & 3], u);
+                                    P[q][j] = __ffma2_rn(w2[q], u, P[q][j]);
+                                }
                             }
                         }
 #pragma unroll
@@ -340,6 +356,7 @@ __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks) path_
     const int n = a.n, ns = a.ns;
     const Smem sm = carve(smem_raw, QP, n, ns, T, a.chunk_rows);
     for (int e = tid; e < n; e += T) sm.c0[e] = a.c0[e];
+    for (int e = tid; e < QP; e += T) reinterpret_cast<float *>(sm.cn)[e] = a.cn[e];
     for (int e = tid; e < 4 * n * ns; e += T) sm.bsum[e] = 0.0;
     // This block's state slot: [R][NST][n][T]; thread tid owns column tid.
     float *st = a.state + (size_t)blockIdx.x * R * NST * n * T + tid;
@@ -385,6 +402,7 @@ __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchArgs b)
             if (tid == 0) sa = b.desc[q];
             __syncthreads();
             for (int e = tid; e < a->n; e += T) sm.c0[e] = a->c0[e];
+            for (int e = tid; e < QP; e += T) reinterpret_cast<float *>(sm.cn)[e] = a->cn[e];
             for (int e = tid; e < 4 * a->n * a->ns; e += T) sm.bsum[e] = 0.0;
         }
         run_tile<SCHEME, QP, 1>(*a, sm, st, b.tile_idx[t]);

@@ -4,8 +4,9 @@
 // products, Eq. (LIBOR-drift-PT) / (bdrift), the Euler step of
 // Eq. (log-LIB-SDE-2) and the payoffs of Eq. (caplet)), mapped differently:
 // lane t of a G-lane group owns path t of the group (its state, increment,
-// weight w, Euler step and payoff) and sweeps the node slice {t, t+G, t+2G,..}
-// of the staged table rows for all G paths of the group.  Each staged table
+// weight w, Euler step and payoff) and sweeps the slice {t, t+G, t+2G,..} of
+// the staged float4 table entries (four nodes each) for all G paths of the
+// group, carrying the scaled products c_j P_j as the one-lane kernel does.  Each staged table
 // value is therefore loaded once per lane and used for G paths, and the
 // compensator A_i of each path is a sum over G lanes (a reduce-scatter by
 // shuffles gives every lane the total of its own path).  The weights w of the
@@ -75,8 +76,9 @@ __device__ __forceinline__ void group_weights(float wown, int t, int gbase, floa
 __host__ __device__ inline size_t group_smem_bytes(int QP, int n, int ns, int threads, int CH)
 {
     size_t b = 0;
-    b += a16(sizeof(float4) * 2 * (size_t)CH * (QP / 2));
+    b += a16(sizeof(float4) * 2 * (size_t)CH * (QP / 4));
     b += a16(sizeof(float4) * 2 * (size_t)CH);
+    b += a16(sizeof(float) * (size_t)QP);
     b += a16(sizeof(float) * (size_t)n);
     b += a16(sizeof(double) * 4 * (size_t)n * ns);
     b += a16(sizeof(double) * 2 * (size_t)(threads / 32) * ns);
@@ -92,10 +94,10 @@ __device__ __forceinline__ void stage(const PathArgs &a, float4 *tab, float4 *ro
     const int ibot = max(imin, itop - CH + 1);
     const int cnt = itop - ibot + 1;
     const size_t r0 = (size_t)k * n + (ibot - 1);
-    constexpr int Q2 = QP / 2;
-    const float4 *src = a.tab + r0 * Q2;
-    float4 *dst = tab + (size_t)b * CH * Q2;
-    for (int e = threadIdx.x; e < cnt * Q2; e += blockDim.x) cp_async16(dst + e, src + e);
+    constexpr int Q4 = QP / 4;
+    const float4 *src = a.tab + r0 * Q4;
+    float4 *dst = tab + (size_t)b * CH * Q4;
+    for (int e = threadIdx.x; e < cnt * Q4; e += blockDim.x) cp_async16(dst + e, src + e);
     for (int e = threadIdx.x; e < cnt; e += blockDim.x) cp_async16(row + b * CH + e, a.row + r0 + e);
 }
 
@@ -105,25 +107,27 @@ template <int SCHEME, int QP, int G>
 __global__ void __launch_bounds__(kMaxThreads, (QP <= 64 ? 2 : 1)) group_kernel(const PathArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int Q2 = QP / 2;     // float4 entries per table row (2 nodes each)
-    constexpr int QL = Q2 / G;     // entries per lane
+    constexpr int Q4 = QP / 4;     // float4 entries per table row (4 nodes each)
+    constexpr int QL = Q4 / G;     // entries per lane
     constexpr int NST = (SCHEME == PICARD) ? 2 : 1;
     const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int t = lane & (G - 1);               // lane within the group = owned path
     const int gbase = lane & ~(G - 1);          // first lane of the group
     const int n = a.n, s = a.s, S = a.S, ns = a.ns, CH = a.chunk_rows;
     float4 *stab, *srow;
-    float *sc0;
+    float *sc0, *scn;
     double *bsum, *red;
     {
         size_t o = 0;
-        stab = reinterpret_cast<float4 *>(smem_raw + o); o += a16(sizeof(float4) * 2 * (size_t)CH * Q2);
+        stab = reinterpret_cast<float4 *>(smem_raw + o); o += a16(sizeof(float4) * 2 * (size_t)CH * Q4);
         srow = reinterpret_cast<float4 *>(smem_raw + o); o += a16(sizeof(float4) * 2 * (size_t)CH);
+        scn = reinterpret_cast<float *>(smem_raw + o); o += a16(sizeof(float) * (size_t)QP);
         sc0 = reinterpret_cast<float *>(smem_raw + o); o += a16(sizeof(float) * (size_t)n);
         bsum = reinterpret_cast<double *>(smem_raw + o); o += a16(sizeof(double) * 4 * (size_t)n * ns);
         red = reinterpret_cast<double *>(smem_raw + o);
     }
     for (int e = tid; e < n; e += T) sc0[e] = a.c0[e];
+    for (int e = tid; e < QP; e += T) scn[e] = a.cn[e];
     for (int e = tid; e < 4 * n * ns; e += T) bsum[e] = 0.0;
 
     // Block slot [NST][n][T]: column = 4 * gidx + t = tid, i.e. this lane's path.
@@ -151,12 +155,18 @@ __global__ void __launch_bounds__(kMaxThreads, (QP <= 64 ? 2 : 1)) group_kernel(
             const int nch = (n - imin + CH) / CH;
             const bool mat = (k + 1) % s == 0;
             const float dH = draw_increment(a, p, (uint32_t)k);
-            // P[q][j]: product for path q of the group, node pair G j + t
-            float2 P[G][QL];
+            // P[q][2j + hf]: scaled product c P of path q of the group, node
+            // pair hf of table entry G j + t
+            float2 P[G][2 * QL];
 #pragma unroll
-            for (int q = 0; q < G; ++q)
+            for (int j = 0; j < QL; ++j) {
+                const float4 cj = reinterpret_cast<const float4 *>(scn)[G * j + t];
 #pragma unroll
-                for (int j = 0; j < QL; ++j) P[q][j] = make_float2(1.0f, 1.0f);
+                for (int q = 0; q < G; ++q) {
+                    P[q][2 * j] = make_float2(cj.x, cj.y);
+                    P[q][2 * j + 1] = make_float2(cj.z, cj.w);
+                }
+            }
             float num = 1.0f, Lm = 0.0f;
 
             for (int c = 0; c < nch; ++c) {
@@ -169,7 +179,7 @@ __global__ void __launch_bounds__(kMaxThreads, (QP <= 64 ? 2 : 1)) group_kernel(
 
                 const int itop = n - c * CH;
                 const int ibot = max(imin, itop - CH + 1);
-                const float4 *tb = stab + (size_t)buf * CH * Q2;
+                const float4 *tb = stab + (size_t)buf * CH * Q4;
                 const float4 *rb = srow + buf * CH;
                 // This lane's state and the group's weights for the first row;
                 // every row then prepares the next row's, so MUFU and shuffle
@@ -193,16 +203,19 @@ __global__ void __launch_bounds__(kMaxThreads, (QP <= 64 ? 2 : 1)) group_kernel(
                                          t, gbase, wn2);
                     }
                     float2 acc[G][2];
-                    const float4 *tr = tb + (size_t)r * Q2 + t;
+                    const float4 *tr = tb + (size_t)r * Q4 + t;
 #pragma unroll
                     for (int j = 0; j < QL; ++j) {
                         const float4 v = tr[G * j];
-                        const float2 e2 = make_float2(v.x, v.y);
-                        const float2 a2 = make_float2(v.z, v.w);
 #pragma unroll
-                        for (int q = 0; q < G; ++q) {
-                            acc[q][j & 1] = (j < 2) ? __fmul2_rn(a2, P[q][j]) : __ffma2_rn(a2, P[q][j], acc[q][j & 1]);
-                            P[q][j] = __ffma2_rn(__fmul2_rn(w2[q], e2), P[q][j], P[q][j]);
+                        for (int hf = 0; hf < 2; ++hf) {
+                            const float2 e2 = hf ? make_float2(v.z, v.w) : make_float2(v.x, v.y);
+#pragma unroll
+                            for (int q = 0; q < G; ++q) {
+                                const float2 u = __fmul2_rn(e2, P[q][2 * j + hf]);
+                                acc[q][hf] = (j == 0) ? u : __fadd2_rn(acc[q][hf], u);
+                                P[q][2 * j + hf] = __ffma2_rn(w2[q], u, P[q][2 * j + hf]);
+                            }
                         }
                     }
                     float part[G];

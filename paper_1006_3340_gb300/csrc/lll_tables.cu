@@ -1,11 +1,12 @@
 // lll_tables.cu -- FP64 precomputation on the GPU and the final reduction.
 //
 // tables_kernel: for every step k and rate l, the node table of the jump
-//   compensator of Eq. (LIBOR-drift-PT): E_lj = e^{lambda_l(t_k) x_j} - 1 and
-//   a_lj = W_j E_lj / x_j^2 (rounded to FP32), and the constant
-//   K_l = C_l - sum_j fl32(a_lj), C_l = sum_j W_j (E_lj - lambda_l x_j) / x_j^2,
-//   so that A_l = K_l + sum_j a_lj P_j reproduces C_l exactly when P = 1.
-//   C_l itself (the compensator with all later weights zero) is kept too.
+//   compensator of Eq. (LIBOR-drift-PT): E_lj = e^{lambda_l(t_k) x_j} - 1
+//   (rounded to FP32), the per-node factors c_j = W_j / x_j^2 (FP32), and the
+//   constant K_l = C_l - sum_j fl32(E_lj c_j) with
+//   C_l = sum_j W_j (E_lj - lambda_l x_j) / x_j^2, so that
+//   A_l = K_l + sum_j E_lj (c_j P_j) reproduces C_l when P = 1 up to the FP32
+//   sum.  C_l itself (the compensator with all later weights zero) is kept too.
 // frozen_drift_kernel: the drift b(t_k, T_l; Z(0)) of Eq. (Picard-2), i.e.
 //   Eq. (LIBOR-drift-PT) with L frozen at L(0), one block per step and one
 //   thread per node, a fixed-order block sum per rate.
@@ -20,26 +21,26 @@ namespace lll {
 namespace {
 
 __global__ void tables_kernel(const double *lam, const double *x, const double *W, int n, int S,
-                              int Q, int QP, float4 *tab, float4 *row, float *Ctab)
+                              int Q, int QP, float4 *tab, float *cn, float4 *row, float *Ctab)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    for (int j = idx; j < QP; j += gridDim.x * blockDim.x)
+        cn[j] = (j < Q) ? (float)(W[j] / (x[j] * x[j])) : 0.0f;
     if (idx >= S * n) return;
     const double li = lam[idx];
     double C = 0.0, sa = 0.0;
-    float *out = reinterpret_cast<float *>(tab + (size_t)idx * (QP / 2));
+    float *out = reinterpret_cast<float *>(tab + (size_t)idx * (QP / 4));
     for (int j = 0; j < QP; ++j) {
-        float e = 0.0f, av = 0.0f;
+        float e = 0.0f;
         if (j < Q) {
             const double xj = x[j];
             const double ed = expm1(li * xj);
             const double inv = W[j] / (xj * xj);
             C += inv * (ed - li * xj);
             e = (float)ed;
-            av = (float)(inv * ed);
-            sa += (double)av;
+            sa += (double)__fmul_rn(e, (float)inv);
         }
-        out[(j >> 1) * 4 + (j & 1)] = e;
-        out[(j >> 1) * 4 + 2 + (j & 1)] = av;
+        out[j] = e;
     }
     float4 r = row[idx];
     r.x = (float)li;
@@ -134,10 +135,10 @@ int batch_finalize(const double *partials, const size_t *seg_off, const int *ins
 }
 
 int launch_tables(const double *lam, const double *x, const double *W, int n, int S, int Q, int QP,
-                  float4 *tab, float4 *row, float *Ctab, cudaStream_t st)
+                  float4 *tab, float *cn, float4 *row, float *Ctab, cudaStream_t st)
 {
     const int total = S * n;
-    tables_kernel<<<(total + 127) / 128, 128, 0, st>>>(lam, x, W, n, S, Q, QP, tab, row, Ctab);
+    tables_kernel<<<(total + 127) / 128, 128, 0, st>>>(lam, x, W, n, S, Q, QP, tab, cn, row, Ctab);
     return (int)cudaGetLastError();
 }
 
