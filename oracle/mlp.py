@@ -12,6 +12,11 @@ products; the GPU's BF16 kernels are compared with it.
 
 Layers: x -> SiLU(x W_1^T + b_1) -> SiLU(. W_2^T + b_2) -> ... -> . w_out + b_out,
 SiLU(z) = z / (1 + e^{-z}); loss = mean (f(x) - y)^2.
+
+simulate_scheme is the full Euler scheme (Eq. (log-LIB-SDE-2), drift of
+Eq. (LIBOR-drift-PT)) whose jump compensator is the network's,
+A_i = C_i + s_y f(x_i), in FP64 on the oracle's own Philox increments; it is
+the definition the GPU's LLL_MLP kernels are compared with path by path.
 """
 from __future__ import annotations
 
@@ -82,6 +87,92 @@ def adam_step(params, grads, state, lr, t, b1=0.9, b2=0.999, eps=1e-8):
             new.append(p - lr * mh / (np.sqrt(vh) + eps))
         out.append(tuple(new))
     return out
+
+
+def bf16_round(a):
+    """Round to the nearest BF16 value (ties to even), returned as FP32: the
+    representation in which the GPU stores the network's weights."""
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    u = a.view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def params_from_flat(flat, offsets, layers, hidden, in_dim, in_pad):
+    """The network held by the GPU as FP64 (W, b) pairs: hidden-layer and
+    output weights as their BF16 values, biases FP32.  ``offsets`` are the
+    flat offsets W_0, b_0, ..., W_{L-1}, b_{L-1}, w_out, b_out."""
+    flat = np.asarray(flat, dtype=np.float32)
+    params = []
+    for l in range(layers):
+        din = in_pad if l == 0 else hidden
+        W = bf16_round(flat[offsets[2 * l]: offsets[2 * l] + hidden * din]).reshape(hidden, din)
+        W = W[:, :in_dim] if l == 0 else W
+        b = flat[offsets[2 * l + 1]: offsets[2 * l + 1] + hidden]
+        params.append((W.astype(np.float64), b.astype(np.float64)))
+    wout = bf16_round(flat[offsets[2 * layers]: offsets[2 * layers] + hidden]).astype(np.float64)[None, :]
+    params.append((wout, flat[offsets[2 * layers + 1]: offsets[2 * layers + 1] + 1].astype(np.float64)))
+    return params
+
+
+def simulate_scheme(model, params, scales, path0=0, npaths=None, strikes=None):
+    """Full Euler scheme with the learned compensator, FP64, paths
+    path0 .. path0 + npaths - 1 of the model's Philox streams.
+
+    Per step k (left point t_k) and live rate i (k < i s):
+      x_i = (t_k s_t, i s_i, lambda(t_k, T_i) s_lam, u_0, u_1, .., u_n),
+      u_m = (log L_m(t_k) - log L_m(0)) s_u (u_0 = 0, the spot rate is fixed),
+      A_i = C_i(t_k) + s_y f(x_i),  C_i = int (e^{lambda_i x} - 1 - lambda_i x) F(dx)
+            (the compensator with every later weight zero, from the oracle's rule),
+      log L_i(t_{k+1}) = log L_i(t_k) - A_i h + lambda_i dH_k,
+    all rates of a step using the state at t_k.  Caplet payoffs at each T_m as
+    in Eq. (caplet).  Returns snap[p, m-1, l-1] = log L_l(T_m) (l >= m) and the
+    payoff sums and prices."""
+    from . import analytic
+    from . import oracle as ora
+
+    wl = model.wl
+    n, s = wl.N - 1, wl.s
+    S, h = n * s, wl.delta / s
+    npaths = wl.paths if npaths is None else int(npaths)
+    strikes = np.asarray(wl.strikes if strikes is None else strikes, dtype=np.float64)
+    ns = strikes.shape[1]
+    s_t, s_i, s_lam, s_u, s_y = (float(v) for v in scales)
+    dH, _ = ora.increments(model, path0, npaths)
+    lam = np.asarray(wl.lam, dtype=np.float64).reshape(S, n)
+    # C_i(t_k): the compensator with every later weight zero, i.e. the rule's
+    # jump cumulant at lambda(t_k, T_i) (entries of rates already fixed,
+    # t_k >= T_i, are never used and may overflow)
+    with np.errstate(over="ignore", invalid="ignore"):
+        C = analytic.kappa_quad(lam.reshape(-1), model.x, model.W).reshape(S, n)
+    logL0 = np.log(np.asarray(wl.L0, dtype=np.float64)[1:])
+    U = np.zeros((npaths, n))
+    snap = np.full((npaths, n, n), np.nan)
+    s1 = np.zeros((n, ns))
+    s2 = np.zeros((n, ns))
+    BN = ora.discount_terminal(wl)
+    for k in range(S):
+        imin = k // s + 1
+        live = np.arange(imin, n + 1)
+        X = np.zeros((npaths, len(live), 3 + wl.N))
+        X[:, :, 0] = k * h * s_t
+        X[:, :, 1] = live * s_i
+        X[:, :, 2] = lam[k, live - 1] * s_lam
+        X[:, :, 4:] = U[:, None, :] * s_u
+        f, _ = forward(params, X.reshape(-1, X.shape[-1]))
+        A = C[k, live - 1][None, :] + s_y * f.reshape(npaths, len(live))
+        U[:, live - 1] += -A * h + lam[k, live - 1][None, :] * dH[:, k:k + 1]
+        if (k + 1) % s == 0:
+            m = imin
+            logL = logL0 + U
+            snap[:, m - 1, m - 1:] = logL[:, m - 1:]
+            num = np.prod(1.0 + wl.delta * np.exp(logL[:, m:]), axis=1)
+            Lm = np.exp(logL[:, m - 1])
+            for q in range(ns):
+                pay = wl.delta * BN * num * np.maximum(Lm - strikes[m - 1, q], 0.0)
+                s1[m - 1, q] = pay.sum()
+                s2[m - 1, q] = (pay * pay).sum()
+    return dict(snap=snap, sum=s1, sumsq=s2, npaths=npaths, **ora.moments(s1, s2, npaths))
 
 
 def adam_state(params):

@@ -1,0 +1,137 @@
+"""Pins of the FP64 oracle of the learned-compensator scheme (oracle.mlp.simulate_scheme).
+
+* A zero network leaves A_i = C_i, the compensator at zero later weights.
+  With one rate (N = 2) the full scheme's compensator is exactly that (the
+  product over later rates is empty), so the scheme must reproduce the C
+  oracle's full scheme.  With tiny initial rates the later weights
+  w_l = delta L_l / (1 + delta L_l) are ~1e-8 and it must agree to ~1e-9.
+* SiLU(z) - SiLU(-z) = z for every z, so a network of any depth can output one
+  input feature exactly (pairs of opposite units).  With f = t s_t, i s_i or
+  lambda_i s_lam the drift moves by a deterministic amount whose sum over the
+  live steps is a closed form; with f = u_n s_u (the last rate's own log-rate
+  offset) the last rate follows a linear recursion around the zero-network
+  path.  These pin every feature column and scale.
+"""
+import dataclasses
+
+import numpy as np
+
+from oracle import mlp
+from oracle import oracle as ora
+from oracle import quadrature
+from paper_1006_3340_gb300 import workloads
+
+SCALES = (0.7, 0.3, 2.0, 5.0, 1e-3)  # s_t, s_i, s_lam, s_u, s_y
+
+
+def _model(wl):
+    x, W = quadrature.rule_for(wl)
+    return ora.OracleModel(wl, x, W)
+
+
+def _zero_net(in_dim, hidden=4, layers=3):
+    params = [(np.zeros((hidden, in_dim)), np.zeros(hidden))]
+    params += [(np.zeros((hidden, hidden)), np.zeros(hidden)) for _ in range(layers - 1)]
+    params.append((np.zeros((1, hidden)), np.zeros(1)))
+    return params
+
+
+def _feature_net(in_dim, j, layers=3):
+    """f(x) = x_j exactly: units (x_j, -x_j), passed on as (h_a - h_b, h_b - h_a)."""
+    W0 = np.zeros((2, in_dim))
+    W0[0, j], W0[1, j] = 1.0, -1.0
+    params = [(W0, np.zeros(2))]
+    P = np.array([[1.0, -1.0], [-1.0, 1.0]])
+    params += [(P.copy(), np.zeros(2)) for _ in range(layers - 1)]
+    params.append((np.array([[1.0, -1.0]]), np.zeros(1)))
+    return params
+
+
+def test_silu_pair_identity_gives_exact_feature():
+    rng = np.random.default_rng(3)
+    x = rng.normal(size=(50, 9)) * 4
+    f, _ = mlp.forward(_feature_net(9, 5), x)
+    assert np.abs(f - x[:, 5]).max() <= 1e-13
+
+
+def test_zero_network_one_rate_is_full_scheme():
+    wl = workloads.tiny(N=2, s=5, Q=8, paths=48)
+    m = _model(wl)
+    got = mlp.simulate_scheme(m, _zero_net(3 + wl.N), SCALES, npaths=wl.paths)
+    ref = ora.simulate(m, ora.FULL, npaths=wl.paths, want_snap=True)
+    assert np.nanmax(np.abs(got["snap"] - ref["snap"])) <= 1e-12
+    assert np.abs(got["price"] - ref["price"]).max() <= 1e-14
+
+
+def test_zero_network_tiny_rates_is_full_scheme():
+    wl = workloads.tiny(N=5, s=3, Q=8, paths=48)
+    wl = dataclasses.replace(wl, L0=np.full(wl.N, 1e-8))
+    m = _model(wl)
+    got = mlp.simulate_scheme(m, _zero_net(3 + wl.N), SCALES, npaths=wl.paths)
+    ref = ora.simulate(m, ora.FULL, npaths=wl.paths, want_snap=True)
+    mask = ~np.isnan(ref["snap"])
+    assert np.array_equal(mask, ~np.isnan(got["snap"]))
+    assert np.abs(got["snap"][mask] - ref["snap"][mask]).max() <= 1e-9
+
+
+def _shift_case(column):
+    wl = workloads.tiny(N=5, s=3, Q=8, paths=16)
+    m = _model(wl)
+    in_dim = 3 + wl.N
+    base = mlp.simulate_scheme(m, _zero_net(in_dim), SCALES, npaths=wl.paths)
+    got = mlp.simulate_scheme(m, _feature_net(in_dim, column), SCALES, npaths=wl.paths)
+    return wl, base["snap"], got["snap"]
+
+
+def test_time_feature_shifts_drift_by_closed_form():
+    wl, base, got = _shift_case(0)
+    s_t, s_y, h = SCALES[0], SCALES[4], wl.h
+    for mat in range(1, wl.n + 1):
+        ks = np.arange(mat * wl.s)
+        shift = -s_y * s_t * h * np.sum(ks * h)
+        d = got[:, mat - 1, mat - 1:] - base[:, mat - 1, mat - 1:]
+        assert np.abs(d - shift).max() <= 1e-13
+
+
+def test_rate_index_feature_shifts_drift_by_closed_form():
+    wl, base, got = _shift_case(1)
+    s_i, s_y, h = SCALES[1], SCALES[4], wl.h
+    for mat in range(1, wl.n + 1):
+        for i in range(mat, wl.n + 1):
+            shift = -s_y * s_i * i * h * (mat * wl.s)
+            d = got[:, mat - 1, i - 1] - base[:, mat - 1, i - 1]
+            assert np.abs(d - shift).max() <= 1e-13
+
+
+def test_volatility_feature_shifts_drift_by_closed_form():
+    wl, base, got = _shift_case(2)
+    s_lam, s_y, h = SCALES[2], SCALES[4], wl.h
+    lam = np.asarray(wl.lam).reshape(wl.steps, wl.n)
+    for mat in range(1, wl.n + 1):
+        for i in range(mat, wl.n + 1):
+            shift = -s_y * s_lam * h * lam[: mat * wl.s, i - 1].sum()
+            d = got[:, mat - 1, i - 1] - base[:, mat - 1, i - 1]
+            assert np.abs(d - shift).max() <= 1e-13
+
+
+def test_last_rate_feature_follows_linear_recursion():
+    """f = u_n s_u: the last rate's offset U obeys
+    U_{k+1} = U_k (1 - s_y s_u h) - C_n h + lambda_n dH_k, the zero-network
+    offset U0 the same without the first term, so D = U - U0 obeys
+    D_{k+1} = D_k - s_y s_u h (D_k + U0_k).  Both offsets are read from the
+    snapshots at the maturities, so the recursion is checked there by
+    re-running it from the zero-network increments."""
+    wl = workloads.tiny(N=4, s=1, Q=8, paths=8)  # one step per period: a snapshot every step
+    m = _model(wl)
+    n = wl.n
+    in_dim = 3 + wl.N
+    col = 3 + n  # u_n
+    base = mlp.simulate_scheme(m, _zero_net(in_dim), SCALES, npaths=wl.paths)["snap"]
+    got = mlp.simulate_scheme(m, _feature_net(in_dim, col), SCALES, npaths=wl.paths)["snap"]
+    s_u, s_y, h = SCALES[3], SCALES[4], wl.h
+    logL0 = np.log(wl.L0[n])
+    U0 = np.concatenate([np.zeros((wl.paths, 1)), base[:, :, n - 1] - logL0], axis=1)  # U0 at t_0 .. t_n
+    D = np.zeros(wl.paths)
+    for k in range(n):
+        D = D - s_y * s_u * h * (D + U0[:, k])
+        assert np.abs((got[:, k, n - 1] - logL0) - (U0[:, k + 1] + D)).max() <= 1e-13
