@@ -199,6 +199,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="library default launch shapes")
+    ap.add_argument("--mlp-kernel", default="auto", choices=["auto", "warp", "tc"],
+                    help="LLL_MLP kernel: tcgen05/TMEM (tc), mma.sync (warp) or the library's choice")
     ap.add_argument("--launch", default="", help="fixed launch shape for the quadrature schemes: "
                     "threads,blocks_per_sm,chunk_rows,paths_per_thread,lanes_per_path (no tuning)")
     args = ap.parse_args()
@@ -238,6 +240,7 @@ def main():
         loss = lll.lll_mlp_train(sims["mlp"].ctx, hidden=128, layers=3, train_paths=1 << 16,
                                  records_per_path=8, epochs=4, batch=8192, lr=2e-3, lr_final=1e-4, seed=7)
         torch.cuda.synchronize()
+        lll.lll_mlp_set_kernel(sims["mlp"].ctx, args.mlp_kernel)
         n_params, in_dim, in_pad, _ = lll.lll_mlp_layout(sims["mlp"].ctx, 3)
         mlp_params = lll.lll_mlp_params(sims["mlp"].ctx, 0, count=n_params)
         mlp_info = {"train_s": time.perf_counter() - t0, "final_loss_scaled": loss, "params": int(n_params),
@@ -361,7 +364,8 @@ def main():
         peak = float(peaks.get("bf16_tflops_sustained", 1679.9))
         return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
                 "traffic": _traffic("mlp/L3/KT3") if wl.paths == 1 << 20 else None,
-                "kernel": "mlp path kernel (mma.sync bf16)",
+                "kernel": ("mlp path kernel (mma.sync bf16)" if args.mlp_kernel == "warp" or wl.N + 3 > 64
+                           else "mlp path kernel (tcgen05 bf16, TMEM accumulators)"),
                 "peak_basis": "bf16_tflops_sustained of MEASURED_PEAKS"}
 
     dom = max(schemes, key=lambda s: statistics.mean(per_scheme_ms[s]))
@@ -386,6 +390,7 @@ def main():
                 if s == "mlp":
                     lll.lll_mlp_init(sim.ctx, 128, 3, 0)
                     lll.lll_mlp_params(sim.ctx, 1, mlp_params[0], scales=mlp_params[1])
+                    lll.lll_mlp_set_kernel(sim.ctx, args.mlp_kernel)
                 lll.lll_simulate(sim.ctx, lll.SCHEMES[s], first, wl.paths, wl.seed)
                 sim.prices()
                 sim.close()

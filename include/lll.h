@@ -264,6 +264,26 @@ int lll_mlp_params(lll_ctx *ctx, int direction, float *params, size_t count, flo
 int lll_mlp_eval(lll_ctx *ctx, const float *x, const float *y, int rows, float *out, float *grads,
                  double *loss);
 
+/* lll_mlp_set_kernel -- which kernel runs LLL_MLP:
+ *   LLL_MLP_KERNEL_AUTO (0, default): the tensor-memory kernel where it
+ *     supports the network, else the warp-level one;
+ *   LLL_MLP_KERNEL_WARP (1): warp-level mma.sync (hidden 128, N <= 61);
+ *   LLL_MLP_KERNEL_TC (2): tcgen05 with TMEM accumulators (hidden 128 and
+ *     2..4 layers with N <= 61, or 2 layers with N <= 125); its waits are
+ *     bounded, and a wait that gives up makes the next read of the results
+ *     return LLL_ETIMEOUT;
+ *   LLL_MLP_KERNEL_LAYERED (3): any network (hidden 256, N up to 125): per
+ *     Euler step, the rows (path, live rate) of a chunk of up to 2^20 rows go
+ *     through the network layer by layer with the training GEMMs; AUTO takes
+ *     it when neither fused kernel fits.
+ * A fused choice the network does not fit returns LLL_EUNSUPPORTED at
+ * simulation. */
+#define LLL_MLP_KERNEL_AUTO 0
+#define LLL_MLP_KERNEL_WARP 1
+#define LLL_MLP_KERNEL_TC 2
+#define LLL_MLP_KERNEL_LAYERED 3
+int lll_mlp_set_kernel(lll_ctx *ctx, int kind);
+
 /* lll_mlp_save / lll_mlp_load -- flat binary file: magic, (hidden, layers,
  * in_dim, N), the five scales, parameter count, FP32 parameters. */
 int lll_mlp_save(lll_ctx *ctx, const char *path);

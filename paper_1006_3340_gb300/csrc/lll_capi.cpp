@@ -64,7 +64,7 @@ void free_all(lll_ctx *c)
     cudaFree(c->d_lam); cudaFree(c->d_x); cudaFree(c->d_W); cudaFree(c->d_w0); cudaFree(c->d_b0);
     cudaFree(c->d_tab); cudaFree(c->d_row); cudaFree(c->d_Z0); cudaFree(c->d_c0);
     cudaFree(c->d_strikes); cudaFree(c->d_partials); cudaFree(c->d_sums); cudaFree(c->d_state);
-    cudaFree(c->d_snap); cudaFree(c->d_C); cudaFree(c->d_cn);
+    cudaFree(c->d_snap); cudaFree(c->d_C); cudaFree(c->d_cn); cudaFree(c->d_err);
     mlp_free(c->mlp);
     c->mlp = nullptr;
     for (auto &e : c->ev)
@@ -401,6 +401,7 @@ int lll_simulate(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, 
     if (e != cudaSuccess) return cuda_fail(ctx, e, "finalize launch");
     CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], ctx->stream));
     ctx->simulated = true;
+    ctx->err_pending = false;
     ctx->last_paths = paths;
     ctx->last_snap_paths = a.n_snap;
     return LLL_OK;
@@ -416,6 +417,14 @@ int lll_get_sums(lll_ctx *ctx, double *sum, double *sumsq, uint64_t *count)
     CUDA_TRY(ctx, cudaMemcpyAsync(buf.data(), ctx->d_sums, sizeof(double) * 2 * cnt,
                                   cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->err_pending && ctx->d_err) {
+        int word = 0;
+        CUDA_TRY(ctx, cudaMemcpy(&word, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (word != 0) {
+            ctx->simulated = false;
+            return fail(ctx, LLL_ETIMEOUT, "a bounded wait of the tensor-core MLP kernel gave up; results discarded");
+        }
+    }
     for (size_t e = 0; e < cnt; ++e) {
         sum[e] = buf[2 * e];
         sumsq[e] = buf[2 * e + 1];

@@ -41,5 +41,8 @@ struct lll_ctx {
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     std::vector<double> lam; // host copy of lambda [S][n]
     lll::MlpState *mlp = nullptr;
+    int mlp_kernel = 0;     // LLL_MLP_KERNEL_*
+    int *d_err = nullptr;   // error word of kernels with bounded waits
+    bool err_pending = false;
     std::string err;
 };

@@ -44,6 +44,8 @@ struct MlpArgs {
     size_t offW[4], offb[4], off_wout, off_bout;
     MlpScales sc;
     const float *Ctab;       // [S][n] compensator at zero weights
+    int in_pad;              // padded input width of layer 0
+    int *err;                // tensor-core kernel: set non-zero when a wait timed out
 };
 
 // lll_mlp_path.cu
@@ -53,5 +55,22 @@ bool mlp_path_supported(int hidden, int layers, int in_pad);
 int mlp_path_occupancy(int layers, int in_pad, size_t smem, int *blocks_per_sm);
 int launch_mlp_path(int layers, int in_pad, int grid, size_t smem, cudaStream_t st, const PathArgs &a,
                     const MlpArgs &g);
+
+// lll_mlp_layered.cu (any network: layer-by-layer over the rows of a step)
+int mlp_layered_threads();
+int launch_mlp_features(const PathArgs &a, const MlpScales &sc, int k, int Pc, const float *state, void *X,
+                        int in_pad, cudaStream_t st);
+int launch_mlp_euler(const PathArgs &a, const float *Ctab, float y_scale, int k, uint64_t chunk_first, int Pc,
+                     float *state, const float *out, double *acc, cudaStream_t st);
+int launch_mlp_acc_to_partials(const double *acc, size_t cells, double *partials, cudaStream_t st);
+
+// lll_mlp_tc.cu (tcgen05, accumulators in tensor memory; hidden = 128)
+int mlp_tc_threads();
+int mlp_tc_paths_per_block();
+size_t mlp_tc_smem(int layers, int in_pad, int n, int ns);
+bool mlp_tc_supported(int hidden, int layers, int in_pad);
+int mlp_tc_occupancy(int layers, int in_pad, size_t smem, int *blocks_per_sm);
+int launch_mlp_tc(int layers, int in_pad, int grid, size_t smem, cudaStream_t st, const PathArgs &a,
+                  const MlpArgs &g);
 
 }  // namespace lll

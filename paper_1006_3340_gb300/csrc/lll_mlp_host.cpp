@@ -50,6 +50,8 @@ struct MlpState {
     size_t split_cap = 0;
     double *d_loss = nullptr;       // per-block loss partials
     int loss_cap = 0;
+    double *d_acc = nullptr;        // layered scheme: per-block Kahan payoff accumulators
+    size_t acc_cap = 0;
 };
 
 void mlp_free_buffers(MlpState *m)
@@ -70,6 +72,7 @@ void mlp_free(MlpState *m)
     if (!m) return;
     mlp_free_buffers(m);
     cudaFree(m->d_p); cudaFree(m->d_g); cudaFree(m->d_m); cudaFree(m->d_v); cudaFree(m->d_ph);
+    cudaFree(m->d_acc);
     delete m;
 }
 
@@ -452,22 +455,114 @@ int lll_mlp_train(lll_ctx *ctx, const lll_mlp_cfg *cfg, double *final_loss)
 
 namespace lll {
 
+// LLL_MLP layer by layer (lll_mlp_layered.cu): any network the training
+// kernels run, paths in chunks whose rows (path, live rate) fit the work
+// buffers.
+int simulate_mlp_layered(lll_ctx *ctx, MlpState *m, uint64_t first_path, uint64_t paths, uint64_t seed)
+{
+    LaunchPlan plan;
+    int rc = plan_launch(ctx, LLL_FULL, first_path, paths, seed, &plan);
+    if (rc != LLL_OK) return rc;
+    const int n = ctx->n, s = ctx->s, S = ctx->S, ns = ctx->ns;
+    const int T = mlp_layered_threads();
+    // chunk of paths: at most 2^20 rows per step, a multiple of the block size
+    const uint64_t rows_cap = 1u << 20;
+    uint64_t Pc = std::max<uint64_t>(T, (rows_cap / (uint64_t)n) / T * T);
+    Pc = std::min<uint64_t>(Pc, (paths + T - 1) / T * T);
+    const int grid = (int)(Pc / T);
+    rc = ensure_rows(ctx, m, (int)(Pc * n));
+    if (rc != LLL_OK) return rc;
+    const size_t state_need = (size_t)n * Pc;
+    if (state_need > ctx->state_cap) {
+        cudaFree(ctx->d_state);
+        ctx->d_state = nullptr;
+        ctx->state_cap = 0;
+        if (cudaMalloc((void **)&ctx->d_state, 4 * state_need) != cudaSuccess) return err(ctx, LLL_ENOMEM, "state");
+        ctx->state_cap = state_need;
+    }
+    const size_t cells = (size_t)grid * n * ns;
+    if (4 * cells > m->acc_cap) {
+        cudaFree(m->d_acc);
+        m->d_acc = nullptr;
+        m->acc_cap = 0;
+        if (cudaMalloc((void **)&m->d_acc, 8 * 4 * cells) != cudaSuccess) return err(ctx, LLL_ENOMEM, "accumulators");
+        m->acc_cap = 4 * cells;
+    }
+    const size_t nout = (size_t)plan.n_out;
+    if ((size_t)grid * nout > ctx->partials_cap) {
+        cudaFree(ctx->d_partials);
+        ctx->d_partials = nullptr;
+        ctx->partials_cap = 0;
+        if (cudaMalloc((void **)&ctx->d_partials, 8 * grid * nout) != cudaSuccess) return err(ctx, LLL_ENOMEM, "partials");
+        ctx->partials_cap = (size_t)grid * nout;
+    }
+    if (nout > ctx->sums_cap) {
+        cudaFree(ctx->d_sums);
+        ctx->d_sums = nullptr;
+        ctx->sums_cap = 0;
+        if (cudaMalloc((void **)&ctx->d_sums, 8 * nout) != cudaSuccess) return err(ctx, LLL_ENOMEM, "sums");
+        ctx->sums_cap = nout;
+    }
+    PathArgs a = plan.args;
+    a.snap = ctx->d_snap; a.snap_stride = ctx->snap_stride; a.snap_pitch = ctx->n_snap;
+    a.n_snap = ctx->d_snap ? std::min<uint64_t>(ctx->n_snap, (paths + ctx->snap_stride - 1) / ctx->snap_stride) : 0;
+    cudaStream_t st = ctx->stream;
+    MTRY(cudaEventRecord(ctx->ev[0], st));
+    MTRY(cudaMemsetAsync(m->d_acc, 0, 8 * 4 * cells, st));
+    for (uint64_t c0 = 0; c0 < paths; c0 += Pc) {
+        MTRY(cudaMemsetAsync(ctx->d_state, 0, 4 * state_need, st));
+        for (int k = 0; k < S; ++k) {
+            const int live = n - (k / s + 1) + 1;
+            MTRY(launch_mlp_features(a, m->sc, k, (int)Pc, ctx->d_state, m->d_X, m->in_pad, st));
+            rc = forward(ctx, m, (int)(Pc * live), nullptr);
+            if (rc != LLL_OK) return rc;
+            MTRY(launch_mlp_euler(a, ctx->d_C, m->sc.y_scale, k, c0, (int)Pc, ctx->d_state, m->d_out, m->d_acc, st));
+        }
+    }
+    MTRY(cudaEventRecord(ctx->ev[1], st));
+    MTRY(launch_mlp_acc_to_partials(m->d_acc, cells, ctx->d_partials, st));
+    MTRY(launch_finalize(ctx->d_partials, grid, (int)nout, ctx->d_sums, st));
+    MTRY(cudaEventRecord(ctx->ev[2], st));
+    ctx->simulated = true;
+    ctx->err_pending = false;
+    ctx->last_paths = paths;
+    ctx->last_snap_paths = a.n_snap;
+    return LLL_OK;
+}
+
 // lll_simulate(LLL_MLP): the full scheme with the network's compensator.
 int simulate_mlp(lll_ctx *ctx, uint64_t first_path, uint64_t paths, uint64_t seed)
 {
     MlpState *m = ctx->mlp;
     if (!m || !m->trained) return err(ctx, LLL_ESTATE, "LLL_MLP needs lll_mlp_train or lll_mlp_load first");
-    if (!mlp_path_supported(m->hidden, m->layers, m->in_pad))
-        return err(ctx, LLL_EUNSUPPORTED, "the fused MLP kernel handles hidden = 128 and N <= 61");
+    const size_t smem_tc = mlp_tc_smem(m->layers, m->in_pad, ctx->n, ctx->ns);
+    const bool tc_ok = mlp_tc_supported(m->hidden, m->layers, m->in_pad) && smem_tc <= 227 * 1024;
+    const bool warp_ok = mlp_path_supported(m->hidden, m->layers, m->in_pad) &&
+                         mlp_path_smem(m->layers, m->in_pad, ctx->n, ctx->ns) <= 227 * 1024;
+    bool use_tc;
+    if (ctx->mlp_kernel == LLL_MLP_KERNEL_TC) {
+        if (!tc_ok) return err(ctx, LLL_EUNSUPPORTED, "the tcgen05 MLP kernel does not support this network");
+        use_tc = true;
+    } else if (ctx->mlp_kernel == LLL_MLP_KERNEL_WARP) {
+        if (!warp_ok) return err(ctx, LLL_EUNSUPPORTED, "the mma.sync MLP kernel handles hidden = 128 and N <= 61");
+        use_tc = false;
+    } else if (ctx->mlp_kernel == LLL_MLP_KERNEL_LAYERED || (!tc_ok && !warp_ok)) {
+        return simulate_mlp_layered(ctx, m, first_path, paths, seed);
+    } else {
+        use_tc = tc_ok;
+    }
     LaunchPlan plan;
     int rc = plan_launch(ctx, LLL_FULL, first_path, paths, seed, &plan);
     if (rc != LLL_OK) return rc;
-    const size_t smem = mlp_path_smem(m->layers, m->in_pad, ctx->n, ctx->ns);
-    if (smem > 227 * 1024) return err(ctx, LLL_EUNSUPPORTED, "MLP kernel shared memory exceeds 227 KB");
+    const size_t smem = use_tc ? smem_tc : mlp_path_smem(m->layers, m->in_pad, ctx->n, ctx->ns);
     int occ = 0;
-    MTRY(mlp_path_occupancy(m->layers, m->in_pad, smem, &occ));
+    if (use_tc) MTRY(mlp_tc_occupancy(m->layers, m->in_pad, smem, &occ));
+    else MTRY(mlp_path_occupancy(m->layers, m->in_pad, smem, &occ));
     if (occ < 1) return err(ctx, LLL_EUNSUPPORTED, "MLP kernel does not fit on an SM");
-    const int T = mlp_path_threads();
+    if (use_tc && !ctx->d_err) {
+        if (cudaMalloc((void **)&ctx->d_err, sizeof(int)) != cudaSuccess) return err(ctx, LLL_ENOMEM, "error word");
+    }
+    const int T = use_tc ? mlp_tc_paths_per_block() : mlp_path_threads();
     const uint64_t tiles = (paths + T - 1) / T;
     const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)occ * ctx->sm_count);
     const size_t state_need = (size_t)grid * ctx->n * T;
@@ -506,8 +601,15 @@ int simulate_mlp(lll_ctx *ctx, uint64_t first_path, uint64_t paths, uint64_t see
     g.off_bout = m->off_bout;
     g.sc = m->sc;
     g.Ctab = ctx->d_C;
+    g.in_pad = m->in_pad;
+    g.err = ctx->d_err;
+    if (use_tc) {
+        MTRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
+        ctx->err_pending = true;
+    }
     MTRY(cudaEventRecord(ctx->ev[0], ctx->stream));
-    MTRY(launch_mlp_path(m->layers, m->in_pad, grid, smem, ctx->stream, a, g));
+    if (use_tc) MTRY(launch_mlp_tc(m->layers, m->in_pad, grid, smem, ctx->stream, a, g));
+    else MTRY(launch_mlp_path(m->layers, m->in_pad, grid, smem, ctx->stream, a, g));
     MTRY(cudaEventRecord(ctx->ev[1], ctx->stream));
     MTRY(launch_finalize(ctx->d_partials, grid, (int)nout, ctx->d_sums, ctx->stream));
     MTRY(cudaEventRecord(ctx->ev[2], ctx->stream));
@@ -520,6 +622,16 @@ int simulate_mlp(lll_ctx *ctx, uint64_t first_path, uint64_t paths, uint64_t see
 }  // namespace lll
 
 extern "C" {
+
+int lll_mlp_set_kernel(lll_ctx *ctx, int kind)
+{
+    if (!ctx) return err(nullptr, LLL_EINVAL, "ctx is NULL");
+    if (kind != LLL_MLP_KERNEL_AUTO && kind != LLL_MLP_KERNEL_WARP && kind != LLL_MLP_KERNEL_TC &&
+        kind != LLL_MLP_KERNEL_LAYERED)
+        return err(ctx, LLL_EINVAL, "unknown MLP kernel");
+    ctx->mlp_kernel = kind;
+    return LLL_OK;
+}
 
 int lll_mlp_save(lll_ctx *ctx, const char *path)
 {

@@ -1,0 +1,154 @@
+// lll_mlp_layered.cu -- the learned-compensator scheme (LLL_MLP) for networks
+// the fused kernels cannot hold (hidden width 256, wide inputs): the network
+// runs layer by layer over all (path, live rate) rows of a step with the
+// training GEMMs, between two small kernels of this file.
+//
+// Per Euler step k of Eq. (log-LIB-SDE-2), for a chunk of paths:
+//  feat_kernel   one BF16 feature row x_i = (t s_t, i s_i, lambda_i s_lam,
+//                u_0 .. u_{N-1}) per (path, live rate), row = p * live + (i - imin);
+//  (network)     f(x) for every row, FP32 (lll_mlp.cu);
+//  euler_kernel  one thread per path: draws Delta H_k, applies
+//                A_i = C_i + s_y f(x_i) (Eq. (LIBOR-drift-PT) with the learned
+//                compensator), records the caplet payoffs of Eq. (caplet) at
+//                T_m into per-block FP64 Kahan accumulators.
+// Blocks own fixed path slots across chunks and steps, so the final
+// block-ordered sum is deterministic.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "lll_device.cuh"
+#include "lll_internal.h"
+#include "lll_mlp.h"
+
+namespace lll {
+namespace {
+
+constexpr int kT = 256; // threads per block of both kernels
+
+__global__ void feat_kernel(const PathArgs a, MlpScales sc, int k, int Pc, const float *state,
+                            __nv_bfloat16 *X, int in_pad)
+{
+    const int n = a.n, imin = k / a.s + 1, live = n - imin + 1;
+    const size_t row = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= (size_t)Pc * live) return;
+    const int p = (int)(row / live), i = imin + (int)(row % live);
+    const float lam = a.row[(size_t)k * n + (i - 1)].x;
+    __nv_bfloat162 *x = reinterpret_cast<__nv_bfloat162 *>(X + row * in_pad);
+    // columns: 0 t, 1 i, 2 lambda_i, 3 u_0 = 0, 3 + m  u_m (m = 1..n), then zeros
+    x[0] = __floats2bfloat162_rn((float)k * a.h * sc.t_scale, (float)i * sc.i_scale);
+    x[1] = __floats2bfloat162_rn(lam * sc.lam_scale, 0.0f);
+    for (int c = 4; c < in_pad; c += 2) {
+        const int m0 = c - 3, m1 = c - 2;
+        const float v0 = m0 <= n ? state[(size_t)(m0 - 1) * Pc + p] * sc.u_scale : 0.0f;
+        const float v1 = m1 <= n ? state[(size_t)(m1 - 1) * Pc + p] * sc.u_scale : 0.0f;
+        x[c / 2] = __floats2bfloat162_rn(v0, v1);
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void kahan_add(double *s, double *c, double x)
+{
+    const double y = x - *c;
+    const double t = *s + y;
+    *c = (t - *s) - y;
+    *s = t;
+}
+
+__global__ void __launch_bounds__(kT) euler_kernel(const PathArgs a, const float *Ctab, float y_scale, int k,
+                                                    uint64_t chunk_first, int Pc, float *state,
+                                                    const float *out, double *acc)
+{
+    __shared__ double red[kT / 32][64][2];
+    const int n = a.n, s = a.s, ns = a.ns, imin = k / s + 1, live = n - imin + 1;
+    const int p = blockIdx.x * kT + threadIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool mat = (k + 1) % s == 0;
+    const uint64_t lp = chunk_first + (uint64_t)p;
+    const bool active = p < Pc && lp < a.paths;
+    float num = 1.0f, Lm = 0.0f;
+    if (p < Pc) {
+        uint64_t sidx = ~0ull;
+        if (a.snap != nullptr && active && lp % a.snap_stride == 0 && lp / a.snap_stride < a.n_snap)
+            sidx = lp / a.snap_stride;
+        const float dH = draw_increment(a, a.first_path + lp, (uint32_t)k);
+        const float h = a.h;
+        for (int i = n; i >= imin; --i) {
+            const size_t rowk = (size_t)k * n + (i - 1);
+            const float A = Ctab[rowk] + y_scale * out[(size_t)p * live + (i - imin)];
+            float *sp = state + (size_t)(i - 1) * Pc + p;
+            const float z = sp[0] + fmaf(a.row[rowk].x, dH, -A * h);
+            sp[0] = z;
+            if (mat) {
+                const float znew = z + a.Z0[i - 1];
+                if (i > imin) num *= fmaf(a.delta, expf(znew), 1.0f);
+                else Lm = expf(znew);
+                if (sidx != ~0ull) a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = znew;
+            }
+        }
+    }
+    if (!mat) return;
+    const int m = imin;
+    for (int q = 0; q < ns; ++q) {
+        const float K = a.strikes[(size_t)(m - 1) * ns + q];
+        const double pay = active ? (double)(a.dBN * num * fmaxf(Lm - K, 0.0f)) : 0.0;
+        const double s1 = warp_sum(pay), s2 = warp_sum(pay * pay);
+        if (lane == 0) {
+            red[warp][q][0] = s1;
+            red[warp][q][1] = s2;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < ns) {
+        double s1 = 0.0, s2 = 0.0;
+        for (int w = 0; w < kT / 32; ++w) {
+            s1 += red[w][threadIdx.x][0];
+            s2 += red[w][threadIdx.x][1];
+        }
+        double *c = acc + 4 * ((size_t)blockIdx.x * n * ns + (size_t)(m - 1) * ns + threadIdx.x);
+        kahan_add(c + 0, c + 1, s1);
+        kahan_add(c + 2, c + 3, s2);
+    }
+}
+
+__global__ void acc_to_partials(const double *acc, size_t cells, double *partials)
+{
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= cells) return;
+    partials[2 * e + 0] = acc[4 * e + 0];
+    partials[2 * e + 1] = acc[4 * e + 2];
+}
+
+}  // namespace
+
+int mlp_layered_threads() { return kT; }
+
+int launch_mlp_features(const PathArgs &a, const MlpScales &sc, int k, int Pc, const float *state, void *X,
+                        int in_pad, cudaStream_t st)
+{
+    const int live = a.n - (k / a.s + 1) + 1;
+    const size_t rows = (size_t)Pc * live;
+    feat_kernel<<<(unsigned)((rows + kT - 1) / kT), kT, 0, st>>>(a, sc, k, Pc, state,
+                                                                  static_cast<__nv_bfloat16 *>(X), in_pad);
+    return (int)cudaGetLastError();
+}
+
+int launch_mlp_euler(const PathArgs &a, const float *Ctab, float y_scale, int k, uint64_t chunk_first, int Pc,
+                     float *state, const float *out, double *acc, cudaStream_t st)
+{
+    if (a.ns > 64) return (int)cudaErrorInvalidValue;
+    euler_kernel<<<(Pc + kT - 1) / kT, kT, 0, st>>>(a, Ctab, y_scale, k, chunk_first, Pc, state, out, acc);
+    return (int)cudaGetLastError();
+}
+
+int launch_mlp_acc_to_partials(const double *acc, size_t cells, double *partials, cudaStream_t st)
+{
+    acc_to_partials<<<(unsigned)((cells + 255) / 256), 256, 0, st>>>(acc, cells, partials);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace lll

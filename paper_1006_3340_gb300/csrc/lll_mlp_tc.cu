@@ -1,0 +1,572 @@
+// lll_mlp_tc.cu -- the full scheme with the learned compensator (LLL_MLP) on
+// the 5th-generation tensor cores (tcgen05, accumulators in tensor memory).
+//
+// Same method as lll_mlp_path.cu: Euler steps of Eq. (log-LIB-SDE-2) with the
+// drift of Eq. (LIBOR-drift-PT), the jump compensator of every live rate being
+// A_i = C_i + s_y f(x_i) with the feature row
+// x_i = (t s_t, i s_i, lambda_i s_lam, u_0 .. u_{N-1}) of the log-rates at t_k
+// and f the trained network (SiLU hidden layers, BF16 weights and
+// activations, FP32 accumulation).
+//
+// Roles of a CTA (544 threads):
+//  * warps 0-15: epilogue.  Warps 8g .. 8g+7 serve path tile g (128 paths,
+//    one per TMEM lane): warp 8g + 4hf + q reads lane quadrant q, columns
+//    64hf .. 64hf+63 of the tile's accumulator, so two threads share a row.
+//    They turn each layer's accumulator into the next layer's BF16 operand
+//    (bias + SiLU) and evaluate their half of the output layer; the hf = 0
+//    thread of a row owns the path: it draws the increments, writes the
+//    feature row, adds the other half's output partial, and makes the Euler
+//    step and the caplet bookkeeping.
+//  * warp 16: allocates 256 TMEM columns (one 128-column accumulator per
+//    tile) and, from one lane, issues the MMAs.  Every layer of every
+//    live rate is one 128 x H x K product D = X W^T (kind::f16, BF16 operands
+//    K-major with 128-byte swizzle in shared memory, FP32 D in TMEM), the
+//    tiles taking turns so that one's epilogue overlaps the other's MMA.
+// Weights stay in shared memory for the whole launch.  Hand-offs use
+// mbarriers: "operand ready" (one arrival per warp of the tile, after every
+// lane's proxy fence), "accumulator ready" (tcgen05.commit) and "output
+// partial ready".  Every wait is bounded: on timeout the CTA sets an
+// error word, abandons its work and releases its tensor memory.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "lll_device.cuh"
+#include "lll_internal.h"
+#include "lll_mlp.h"
+
+namespace lll {
+namespace {
+
+constexpr int kH = 128;               // hidden width
+constexpr int kRows = 128;            // rows (paths) per warpgroup tile
+constexpr int kGroups = 2;            // path tiles in flight per CTA
+constexpr int kEpiWarps = 8 * kGroups; // per tile: 4 lane quadrants x 2 column halves
+constexpr int kThreads = (kEpiWarps + 1) * 32;
+constexpr int kTileBytes = kRows * 128; // one 64-wide K block of a 128-row operand
+constexpr long long kWaitBudget = 4000000000ll; // clock cycles (about 2 s)
+
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t a)
+{
+    return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = kH.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH >> 3) << 17) |
+                            ((uint32_t)(kRows >> 4) << 24);
+
+// Byte offset of the 16-byte chunk c8 (0..7) of K block kb in row r of a 128-row operand.
+__device__ __forceinline__ uint32_t chunk_off(int r, int kb, int c8)
+{
+    return (uint32_t)(kb * kTileBytes + (r >> 3) * 1024 + (r & 7) * 128 + ((c8 ^ (r & 7)) << 4));
+}
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi)
+{
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__device__ __forceinline__ float tanh_approx(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
+}
+
+// Wait for the completion of the phase of parity `par`.  Gives up when the
+// CTA's abort word is set or after kWaitBudget cycles (then sets it, and the
+// launch's error word).
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t par, volatile int *abort, int *err)
+{
+    const uint32_t a = saddr(b);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok)
+                     : "r"(a), "r"(par)
+                     : "memory");
+        if (ok) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > kWaitBudget) {
+            *abort = 1;
+            atomicOr(err, 1);
+            return false;
+        }
+    }
+}
+
+// The same, decided once per warp (lane 0 polls) so that all lanes leave a
+// loop together before any .sync.aligned tcgen05 instruction.
+__device__ __forceinline__ bool warp_wait(uint64_t *b, uint32_t par, volatile int *abort, int *err)
+{
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(b, par, abort, err) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp(); // orders the other lanes after lane 0's acquire
+    return ok != 0;
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                 "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *b)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(b))
+                 : "memory");
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane: the
+// load is issued by tmem_ld32 and its registers become valid at tmem_wait32,
+// which takes them as in/out operands so that no use is scheduled before it.
+#define LLL_R32(r) "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), \
+    "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),           \
+    "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),         \
+    "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+
+__device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                   "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                   "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(ta));
+}
+
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : LLL_R32(r) : : "memory");
+}
+
+// Bias + SiLU of 8 accumulator values: with z = v + b and hz = z / 2 (from
+// the half bias hb), SiLU(z) = z sigma(z) = hz + hz tanh(hz), the same
+// function as the training kernels' z (1 + tanh(z / 2)) / 2 (one MUFU
+// operation and two f32x2 FMAs per pair).
+__device__ __forceinline__ void silu8(const uint32_t *v, const float *hb, float (&sv)[8])
+{
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+        const float2 hz = __ffma2_rn(make_float2(__uint_as_float(v[e]), __uint_as_float(v[e + 1])),
+                                     make_float2(0.5f, 0.5f), make_float2(hb[e], hb[e + 1]));
+        const float2 t = make_float2(tanh_approx(hz.x), tanh_approx(hz.y));
+        const float2 r = __ffma2_rn(hz, t, hz);
+        sv[e] = r.x;
+        sv[e + 1] = r.y;
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ void kahan_add(double *s, double *c, double x)
+{
+    const double y = x - *c;
+    const double t = *s + y;
+    *c = (t - *s) - y;
+    *s = t;
+}
+
+// Shared-memory plan; operand tiles first (1024-byte aligned).
+struct TcLayout {
+    uint32_t w0, w, u, x, bias, wout, bars, misc, opart, red, bsum, total;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int L, int KB0, int n, int ns)
+{
+    TcLayout t;
+    uint32_t o = 0;
+    t.w0 = o; o += KB0 * kTileBytes;             // W_0: H rows x 64 KB0 columns
+    t.w = o; o += (L - 1) * 2 * kTileBytes;       // W_1 .. W_{L-1}: H rows x 128 columns
+    t.u = o; o += kGroups * KB0 * kTileBytes;     // feature rows, per tile
+    t.x = o; o += kGroups * 2 * kTileBytes;       // hidden activations, per tile
+    t.bias = o; o += L * kH * 4;                  // b_0 / 2 .. b_{L-1} / 2
+    t.wout = o; o += kH * 4;                      // output weights (BF16 values)
+    t.bars = o; o += 10 * 8;                      // mbarriers
+    t.misc = o; o += 16;                          // TMEM base, abort word
+    t.opart = o; o += kGroups * kRows * 4;        // output partial of the upper column half
+    o = (o + 15) & ~15u;
+    t.red = o; o += 2 * (kEpiWarps / 2) * ns * 2 * 8; // per-warp payoff sums, two buffers
+    t.bsum = o; o += n * ns * 4 * 8;              // Kahan accumulators
+    t.total = o + 1024;                           // slack for aligning the base
+    return t;
+}
+
+template <int L, int KB0>
+__global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, const MlpArgs g)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sm = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);
+    const int n = a.n, s = a.s, S = a.S, ns = a.ns;
+    const TcLayout lay = tc_layout(L, KB0, n, ns);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sbase = saddr(sm);
+    float *bias = reinterpret_cast<float *>(sm + lay.bias);
+    float *wout = reinterpret_cast<float *>(sm + lay.wout);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + lay.bars);
+    uint64_t *opb = bars + 0;  // [kGroups] operand ready (one arrival per warp of the tile)
+    uint64_t *dnb = bars + 2;  // [kGroups] accumulator ready (commit)
+    uint64_t *outb = bars + 4; // [kGroups] upper-half output partials written (4 arrivals)
+    uint64_t *payb = bars + 6; // payoff partials written (one arrival per path-owning warp)
+    uint64_t *finb = bars + 7; // all MMAs complete (commit)
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + lay.misc);
+    volatile int *abort = reinterpret_cast<volatile int *>(sm + lay.misc + 4);
+    float *opart = reinterpret_cast<float *>(sm + lay.opart);
+    double *red = reinterpret_cast<double *>(sm + lay.red);
+    double *bsum = reinterpret_cast<double *>(sm + lay.bsum);
+    const int in_pad = KB0 * 64 >= g.in_pad ? g.in_pad : KB0 * 64;
+
+    // ---- stage the weights into the swizzled operand layout ----
+    for (int l = 0; l < L; ++l) {
+        const int din = l == 0 ? in_pad : kH;
+        const int chunks = l == 0 ? KB0 * 8 : 16; // 16-byte chunks per row
+        const __nv_bfloat16 *W = g.wh + g.offW[l];
+        const uint32_t base = l == 0 ? lay.w0 : lay.w + (l - 1) * 2 * kTileBytes;
+        for (int e = tid; e < kH * chunks; e += kThreads) {
+            const int h = e / chunks, c = e % chunks;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (c * 8 < din) v = *reinterpret_cast<const uint4 *>(W + (size_t)h * din + c * 8);
+            *reinterpret_cast<uint4 *>(sm + base + chunk_off(h, c >> 3, c & 7)) = v;
+        }
+    }
+    for (int e = tid; e < L * kH; e += kThreads) bias[e] = 0.5f * g.wp[g.offb[e / kH] + e % kH]; // half biases
+    for (int e = tid; e < kH; e += kThreads) wout[e] = __bfloat162float(g.wh[g.off_wout + e]);
+    for (int e = tid; e < 4 * n * ns; e += kThreads) bsum[e] = 0.0;
+    if (tid == 0) {
+        for (int gi = 0; gi < kGroups; ++gi) {
+            mbar_init(&opb[gi], 8);   // the 8 warps of the tile
+            mbar_init(&dnb[gi], 1);
+            mbar_init(&outb[gi], 4);  // the 4 upper-half warps
+        }
+        mbar_init(payb, kEpiWarps / 2);
+        mbar_init(finb, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_async_smem();
+    if (warp == kEpiWarps) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
+                     "r"(kGroups * kH));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = *tslot;
+    const uint64_t ntiles = (a.paths + kGroups * kRows - 1) / (kGroups * kRows);
+
+    if (warp == kEpiWarps) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            uint32_t ph[kGroups] = {0, 0};
+            bool ok = true;
+            for (uint64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+                for (int k = 0; ok && k < S; ++k) {
+                    const int live = n - (k / s + 1) + 1;
+                    for (int r = 0; ok && r < live; ++r) {
+                        for (int l = 0; ok && l < L; ++l) {
+                            for (int gi = 0; gi < kGroups; ++gi) {
+                                if (!mbar_wait(&opb[gi], ph[gi], abort, g.err)) { ok = false; break; }
+                                ph[gi] ^= 1;
+                                tc_after();
+                                const uint32_t d = tmem + gi * kH;
+                                const uint32_t abase = sbase + (l == 0 ? lay.u + gi * KB0 * kTileBytes
+                                                                       : lay.x + gi * 2 * kTileBytes);
+                                const uint32_t bbase = sbase + (l == 0 ? lay.w0 : lay.w + (l - 1) * 2 * kTileBytes);
+                                const int ks_n = l == 0 ? in_pad / 16 : kH / 16;
+                                for (int ks = 0; ks < ks_n; ++ks) {
+                                    const uint32_t off = (ks >> 2) * kTileBytes + (ks & 3) * 32;
+                                    mma_bf16(d, sdesc(abase + off), sdesc(bbase + off), ks > 0);
+                                }
+                                mma_commit(&dnb[gi]);
+                            }
+                        }
+                    }
+                }
+            }
+            // drain: the commit below completes only after every MMA issued above
+            mma_commit(finb);
+            volatile int dummy_abort = 0;
+            mbar_wait(finb, 0, &dummy_abort, g.err);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- epilogue warps ----------------
+        // warp = 8 gi + 4 hf + q4: tile gi, column half hf (columns 64 hf .. 64 hf + 63),
+        // TMEM lane quadrant q4.  The hf = 0 thread of a row owns the path.
+        const int gi = warp >> 3, hf = (warp >> 2) & 1, q4 = warp & 3;
+        const int row = q4 * 32 + lane;          // TMEM lane = tile row
+        const int T = kGroups * kRows;           // paths per CTA tile
+        const int col = gi * kRows + row;        // column of this path in the state slot
+        const bool owner = hf == 0;
+        const int owarp = gi * 4 + q4;           // index of a path-owning warp
+        unsigned char *xptr = sm + lay.x + gi * 2 * kTileBytes;
+        const uint32_t dcol = tmem + ((uint32_t)(q4 * 32) << 16) + gi * kH + hf * 64;
+        float *st = a.state + (size_t)blockIdx.x * n * T + col;
+        const float h = a.h, delta = a.delta;
+        const float b_out = g.wp[g.off_bout];
+        uint32_t phd = 0, pho = 0, php = 0;
+        int mcount = 0;
+        bool ok = true;
+        for (uint64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+            const uint64_t lp = tile * (uint64_t)T + col;
+            const bool active = lp < a.paths;
+            const uint64_t p = a.first_path + lp;
+            uint64_t sidx = ~0ull;
+            if (owner && a.snap != nullptr && active && lp % a.snap_stride == 0 && lp / a.snap_stride < a.n_snap)
+                sidx = lp / a.snap_stride;
+            if (owner)
+                for (int l = 0; l < n; ++l) st[(size_t)l * T] = 0.0f;
+
+            for (int k = 0; ok && k < S; ++k) {
+                const int imin = k / s + 1;
+                const bool mat = (k + 1) % s == 0;
+                float dH = 0.0f;
+                uint32_t u14[2] = {0, 0}; // BF16 u_1 .. u_4 (columns 4 .. 7)
+                const float xt = (float)k * h * g.sc.t_scale;
+                if (owner) {
+                    dH = draw_increment(a, p, (uint32_t)k);
+                    // feature row of this path at t_k: u_m at column 3 + m (u_0 = 0)
+                    for (int c8 = 1; c8 < KB0 * 8; ++c8) {
+                        float f[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int m = c8 * 8 + e - 3;
+                            f[e] = (m >= 1 && m <= n) ? st[(size_t)(m - 1) * T] * g.sc.u_scale : 0.0f;
+                        }
+                        *reinterpret_cast<uint4 *>(sm + lay.u + gi * KB0 * kTileBytes + chunk_off(row, c8 >> 3, c8 & 7)) =
+                            make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+                    }
+                    float f[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) f[e] = (e + 1 <= n) ? st[(size_t)e * T] * g.sc.u_scale : 0.0f;
+                    u14[0] = pack2(f[0], f[1]);
+                    u14[1] = pack2(f[2], f[3]);
+                }
+                float num = 1.0f, Lm = 0.0f;
+                float lam_c = 0.0f, C_c = 0.0f;
+                if (owner) {
+                    lam_c = a.row[(size_t)k * n + (n - 1)].x;
+                    C_c = g.Ctab[(size_t)k * n + (n - 1)];
+                }
+                for (int i = n; ok && i >= imin; --i) {
+                    const size_t rowk = (size_t)k * n + (i - 1);
+                    float *sp = st + (size_t)(i - 1) * T;
+                    float zold = 0.0f, lam_n = 0.0f, C_n = 0.0f;
+                    if (owner) {
+                        zold = sp[0];
+                        if (i > imin) {
+                            lam_n = a.row[rowk - 1].x;
+                            C_n = g.Ctab[rowk - 1];
+                        }
+                        // columns 0..7: t, i, lambda_i, u_0 = 0, u_1 .. u_4
+                        *reinterpret_cast<uint4 *>(sm + lay.u + gi * KB0 * kTileBytes + chunk_off(row, 0, 0)) =
+                            make_uint4(pack2(xt, (float)i * g.sc.i_scale), pack2(lam_c * g.sc.lam_scale, 0.0f),
+                                       u14[0], u14[1]);
+                    }
+                    fence_async_smem();
+                    tc_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&opb[gi]);
+                    float o4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+                    for (int l = 0; l < L; ++l) {
+                        if (!warp_wait(&dnb[gi], phd, abort, g.err)) { ok = false; break; }
+                        phd ^= 1;
+                        tc_after();
+                        const float *hbl = bias + l * kH + hf * 64;
+                        uint32_t ra[32], rb[32];
+                        tmem_ld32(dcol, ra);
+                        tmem_wait32(ra);
+                        tmem_ld32(dcol + 32, rb);
+#pragma unroll
+                        for (int cc = 0; cc < 2; ++cc) {
+                            const uint32_t *cur = cc ? rb : ra;
+                            if (cc == 1) tmem_wait32(rb);
+#pragma unroll
+                            for (int qd = 0; qd < 4; ++qd) {
+                                float sv[8];
+                                silu8(cur + qd * 8, hbl + cc * 32 + qd * 8, sv);
+                                if (l < L - 1) {
+                                    // columns 64 hf + 32 cc + 8 qd .. +7: K block hf, chunk 4 cc + qd
+                                    *reinterpret_cast<uint4 *>(xptr + chunk_off(row, hf, cc * 4 + qd)) =
+                                        make_uint4(pack2(sv[0], sv[1]), pack2(sv[2], sv[3]), pack2(sv[4], sv[5]),
+                                                   pack2(sv[6], sv[7]));
+                                } else {
+                                    const float *wo = wout + hf * 64 + cc * 32 + qd * 8;
+#pragma unroll
+                                    for (int e = 0; e < 8; e += 2) {
+                                        // BF16 activations (packed round to nearest even), FP32 products
+                                        const uint32_t pk = pack2(sv[e], sv[e + 1]);
+                                        o4[e & 3] = fmaf(__uint_as_float(pk << 16), wo[e], o4[e & 3]);
+                                        o4[(e + 1) & 3] = fmaf(__uint_as_float(pk & 0xffff0000u), wo[e + 1], o4[(e + 1) & 3]);
+                                    }
+                                }
+                            }
+                        }
+                        if (l < L - 1) {
+                            fence_async_smem();
+                            tc_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&opb[gi]);
+                        }
+                    }
+                    if (!ok) break;
+                    const float opart_own = (o4[0] + o4[1]) + (o4[2] + o4[3]);
+                    if (!owner) {
+                        opart[gi * kRows + row] = opart_own;
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&outb[gi]);
+                        continue;
+                    }
+                    // Euler step of this path with A_i = C_i + s_y f
+                    if (!warp_wait(&outb[gi], pho, abort, g.err)) { ok = false; break; }
+                    pho ^= 1;
+                    const float o = opart_own + opart[gi * kRows + row];
+                    const float A = C_c + g.sc.y_scale * (o + b_out);
+                    const float z = zold + fmaf(lam_c, dH, -A * h);
+                    sp[0] = z;
+                    if (mat) {
+                        const float znew = z + a.Z0[i - 1];
+                        if (i > imin) num *= fmaf(delta, expf(znew), 1.0f);
+                        else Lm = expf(znew);
+                        if (sidx != ~0ull) a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = znew;
+                    }
+                    lam_c = lam_n;
+                    C_c = C_n;
+                }
+                if (!ok) break;
+                if (mat && owner) {
+                    const int m = imin, buf = mcount & 1;
+                    ++mcount;
+                    for (int qs = 0; qs < ns; ++qs) {
+                        const float K = a.strikes[(size_t)(m - 1) * ns + qs];
+                        const double pay = active ? (double)(a.dBN * num * fmaxf(Lm - K, 0.0f)) : 0.0;
+                        const double s1 = warp_sum(pay);
+                        const double s2 = warp_sum(pay * pay);
+                        if (lane == 0) {
+                            red[(((size_t)buf * (kEpiWarps / 2) + owarp) * ns + qs) * 2 + 0] = s1;
+                            red[(((size_t)buf * (kEpiWarps / 2) + owarp) * ns + qs) * 2 + 1] = s2;
+                        }
+                    }
+                    if (lane == 0) mbar_arrive(payb);
+                    if (warp == 0) {
+                        // all path-owning warps have written this maturity's sums
+                        if (!warp_wait(payb, php, abort, g.err)) { ok = false; break; }
+                    }
+                    if (tid == 0) {
+                        for (int qs = 0; qs < ns; ++qs) {
+                            double s1 = 0.0, s2 = 0.0;
+                            for (int wv = 0; wv < kEpiWarps / 2; ++wv) {
+                                s1 += red[(((size_t)buf * (kEpiWarps / 2) + wv) * ns + qs) * 2 + 0];
+                                s2 += red[(((size_t)buf * (kEpiWarps / 2) + wv) * ns + qs) * 2 + 1];
+                            }
+                            double *acc = bsum + 4 * ((size_t)(m - 1) * ns + qs);
+                            kahan_add(acc + 0, acc + 1, s1);
+                            kahan_add(acc + 2, acc + 3, s2);
+                        }
+                    }
+                    php ^= 1;
+                }
+            }
+        }
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == kEpiWarps) {
+        tc_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kGroups * kH));
+    }
+    double *out = a.partials + (size_t)blockIdx.x * n * ns * 2;
+    for (int e = tid; e < n * ns; e += kThreads) {
+        out[2 * e + 0] = bsum[4 * e + 0];
+        out[2 * e + 1] = bsum[4 * e + 2];
+    }
+}
+
+typedef void (*TcKernelFn)(const PathArgs, const MlpArgs);
+
+TcKernelFn pick_tc(int L, int KB0)
+{
+    if (KB0 == 1) {
+        switch (L) {
+        case 2: return mlp_tc_kernel<2, 1>;
+        case 3: return mlp_tc_kernel<3, 1>;
+        case 4: return mlp_tc_kernel<4, 1>;
+        default: return nullptr;
+        }
+    }
+    if (KB0 == 2) {
+        switch (L) {
+        case 2: return mlp_tc_kernel<2, 2>;
+        default: return nullptr;
+        }
+    }
+    return nullptr;
+}
+
+}  // namespace
+
+int mlp_tc_threads() { return kThreads; }
+int mlp_tc_paths_per_block() { return kGroups * kRows; }
+
+size_t mlp_tc_smem(int layers, int in_pad, int n, int ns)
+{
+    return tc_layout(layers, (in_pad + 63) / 64, n, ns).total;
+}
+
+bool mlp_tc_supported(int hidden, int layers, int in_pad)
+{
+    return hidden == kH && in_pad % 16 == 0 && pick_tc(layers, (in_pad + 63) / 64) != nullptr;
+}
+
+int mlp_tc_occupancy(int layers, int in_pad, size_t smem, int *blocks_per_sm)
+{
+    TcKernelFn f = pick_tc(layers, (in_pad + 63) / 64);
+    if (!f) return (int)cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kThreads, smem);
+}
+
+int launch_mlp_tc(int layers, int in_pad, int grid, size_t smem, cudaStream_t st, const PathArgs &a,
+                  const MlpArgs &g)
+{
+    TcKernelFn f = pick_tc(layers, (in_pad + 63) / 64);
+    if (!f) return (int)cudaErrorInvalidValue;
+    f<<<grid, kThreads, smem, st>>>(a, g);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace lll

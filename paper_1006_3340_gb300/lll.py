@@ -86,6 +86,7 @@ def load():
         "lll_mlp_eval": (I, [V, _fp, _fp, I, _fp, _fp, _dp]),
         "lll_mlp_save": (I, [V, ctypes.c_char_p]),
         "lll_mlp_load": (I, [V, ctypes.c_char_p]),
+        "lll_mlp_set_kernel": (I, [V, I]),
         "lll_batch_init": (I, [ctypes.POINTER(V), I, ctypes.POINTER(lll_instance), V]),
         "lll_batch_set_launch": (I, [V, I, I, I]),
         "lll_batch_use_graph": (I, [V, I]),
@@ -255,6 +256,14 @@ def lll_mlp_save(ctx, path):
 
 def lll_mlp_load(ctx, path):
     _check(load().lll_mlp_load(ctx, str(path).encode()), ctx)
+
+
+MLP_KERNELS = {"auto": 0, "warp": 1, "tc": 2, "layered": 3}
+
+
+def lll_mlp_set_kernel(ctx, kind):
+    """Kernel of LLL_MLP: "auto", "warp" (mma.sync), "tc" (tcgen05 + TMEM) or "layered"."""
+    _check(load().lll_mlp_set_kernel(ctx, MLP_KERNELS[kind] if isinstance(kind, str) else int(kind)), ctx)
 
 
 def lll_batch_init(instances, stream: int = 0):

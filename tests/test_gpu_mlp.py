@@ -160,3 +160,123 @@ def test_mlp_scheme_against_fp64_oracle(lll, trained):
     p_mlp, _ = sim.prices()
     ref = ora.simulate(ora.OracleModel(wl, x, W), ora.FULL, npaths=cnt)
     assert np.abs(p_mlp - ref["price"]).max() <= 5e-5  # 0.5 bp of notional
+
+
+def test_tcgen05_kernel_matches_mma_sync_kernel(lll, trained):
+    """The tensor-memory kernel and the warp-level kernel evaluate the same
+    network on the same paths: BF16 activations, FP32 accumulation in a
+    different order.  A rounding difference moves one activation by at most
+    2^-8 relative, which moves a drift by a small fraction of s_y; over the
+    312 steps the log-rates then agree to 2e-6 and the prices to 1e-9."""
+    wl, x, W, sim, loss = trained
+    cnt = 4096
+    try:
+        lll.lll_mlp_set_kernel(sim.ctx, "warp")
+        p_w, _, z_w = _run(sim, "mlp", cnt)
+        lll.lll_mlp_set_kernel(sim.ctx, "tc")
+        p_t, _, z_t = _run(sim, "mlp", cnt)
+        sim.simulate("mlp", paths=wl.paths)  # full launch shape, ragged-free 2^16 paths
+        lll.lll_mlp_set_kernel(sim.ctx, "warp")
+        sim.simulate("mlp", paths=wl.paths - 77)  # ragged last tile
+        p_wr, _ = sim.prices()
+        lll.lll_mlp_set_kernel(sim.ctx, "tc")
+        sim.simulate("mlp", paths=wl.paths - 77)
+        p_tr, _ = sim.prices()
+    finally:
+        lll.lll_mlp_set_kernel(sim.ctx, "auto")
+    mask = ~np.isnan(z_w)
+    assert np.abs(z_t[mask] - z_w[mask]).max() <= 2e-6
+    assert np.abs(p_t - p_w).max() <= 1e-9
+    assert np.abs(p_tr - p_wr).max() <= 1e-9
+
+
+@pytest.fixture(scope="module")
+def fp64_scheme(lll, trained):
+    """The FP64 oracle of the scheme with the trained network, first 24 paths."""
+    wl, x, W, sim, loss = trained
+    n_params, in_dim, in_pad, offs = lll.lll_mlp_layout(sim.ctx, L)
+    flat, scales = lll.lll_mlp_params(sim.ctx, 0, count=n_params)
+    params = omlp.params_from_flat(flat, offs, L, H, in_dim, in_pad)
+    return scales, omlp.simulate_scheme(ora.OracleModel(wl, x, W), params, scales, npaths=24)
+
+
+@pytest.mark.parametrize("kind", ["tc", "warp", "layered"])
+def test_mlp_kernels_match_fp64_scheme_path_by_path(lll, trained, fp64_scheme, kind):
+    """Both LLL_MLP kernels against the FP64 oracle of the same scheme with the
+    same (BF16-stored) network, on identical Philox increments.  The GPU feeds
+    BF16 features and activations through the network, so one evaluation of f
+    may differ from the FP64 one by a few per cent of its unit RMS (the forward
+    test's bound, 2e-2 of max |f|, plus the SiLU approximation); a log-rate
+    offset integrates h s_y times that over at most T_N / h steps:
+    |d log L| <= T_N s_y 0.05."""
+    wl, x, W, sim, loss = trained
+    cnt = 24
+    scales, ref = fp64_scheme
+    try:
+        lll.lll_mlp_set_kernel(sim.ctx, kind)
+        sim.simulate("mlp", paths=cnt, snapshots=cnt)
+        z = sim.paths(0, cnt).astype(np.float64)
+        p, _ = sim.prices()
+    finally:
+        lll.lll_mlp_set_kernel(sim.ctx, "auto")
+    mask = ~np.isnan(ref["snap"])
+    assert np.array_equal(mask, ~np.isnan(z))
+    tol = wl.N * wl.delta * float(scales[4]) * 0.05
+    err = np.abs(z[mask] - ref["snap"][mask]).max()
+    assert err <= tol, (err, tol)
+    # payoff sensitivity to a log-rate: delta B(0,T_N) L (1 + delta L)^n < 1e-2
+    assert np.abs(p - ref["price"]).max() <= 1e-2 * tol
+
+
+def test_layered_path_matches_fused_kernel(lll, trained):
+    """The layer-by-layer path (training GEMMs over all rows of a step) and the
+    fused tensor-memory kernel evaluate the same network on the same paths."""
+    wl, x, W, sim, loss = trained
+    cnt = 4096
+    try:
+        lll.lll_mlp_set_kernel(sim.ctx, "tc")
+        p_t, _, z_t = _run(sim, "mlp", cnt)
+        lll.lll_mlp_set_kernel(sim.ctx, "layered")
+        p_l, _, z_l = _run(sim, "mlp", cnt)
+        sim.simulate("mlp", paths=wl.paths - 77)  # several chunks' worth of rows, ragged end
+        p_lr, _ = sim.prices()
+        lll.lll_mlp_set_kernel(sim.ctx, "tc")
+        sim.simulate("mlp", paths=wl.paths - 77)
+        p_tr, _ = sim.prices()
+    finally:
+        lll.lll_mlp_set_kernel(sim.ctx, "auto")
+    mask = ~np.isnan(z_t)
+    assert np.abs(z_l[mask] - z_t[mask]).max() <= 2e-6
+    assert np.abs(p_l - p_t).max() <= 1e-9
+    assert np.abs(p_lr - p_tr).max() <= 1e-9
+
+
+def test_wide_network_on_long_dated_workload_matches_fp64_scheme(lll):
+    """The N=120 workload with the 123 -> 4 x 256 -> 1 network (no fused kernel
+    holds it: LLL_MLP runs layer by layer).  Any network defines a scheme, so
+    a seeded random one with a small output unit s_y is checked path by path
+    against the FP64 oracle of the scheme."""
+    wl = workloads.long_dated(paths=2)
+    x, W = quadrature.rule_for(wl)
+    sim = lll.LevyLibor(wl, x, W)
+    try:
+        lll.lll_mlp_init(sim.ctx, 256, 4, seed=21)
+        n_params, in_dim, in_pad, offs = lll.lll_mlp_layout(sim.ctx, 4)
+        assert (in_dim, in_pad) == (123, 128)
+        flat, scales = lll.lll_mlp_params(sim.ctx, 0, count=n_params)
+        scales = np.array(scales, dtype=np.float32)
+        scales[4] = 2e-4  # s_y: drift perturbation of the order of the learned part
+        lll.lll_mlp_params(sim.ctx, 1, flat, scales=scales)
+        sim.simulate("mlp", paths=wl.paths, snapshots=wl.paths)
+        z = sim.paths(0, wl.paths).astype(np.float64)
+        p, _ = sim.prices()
+    finally:
+        sim.close()
+    params = omlp.params_from_flat(flat, offs, 4, 256, in_dim, in_pad)
+    ref = omlp.simulate_scheme(ora.OracleModel(wl, x, W), params, scales, npaths=wl.paths)
+    mask = ~np.isnan(ref["snap"])
+    assert np.array_equal(mask, ~np.isnan(z))
+    tol = wl.N * wl.delta * float(scales[4]) * 0.05
+    err = np.abs(z[mask] - ref["snap"][mask]).max()
+    assert err <= tol, (err, tol)
+    assert np.abs(p - ref["price"]).max() <= 1e-2 * tol
