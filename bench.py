@@ -363,7 +363,8 @@ def main():
         ach = units * 2 * macs / (ms * 1e-3) / 1e12
         peak = float(peaks.get("bf16_tflops_sustained", 1679.9))
         return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": _traffic("mlp/L3/KT3") if wl.paths == 1 << 20 else None,
+                "traffic": (_traffic("mlp/L3/KT3" if args.mlp_kernel == "warp" else "mlp_tc/L3/KB1")
+                            if wl.paths == 1 << 20 else None),
                 "kernel": ("mlp path kernel (mma.sync bf16)" if args.mlp_kernel == "warp" or wl.N + 3 > 64
                            else "mlp path kernel (tcgen05 bf16, TMEM accumulators)"),
                 "peak_basis": "bf16_tflops_sustained of MEASURED_PEAKS"}

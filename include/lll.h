@@ -44,8 +44,20 @@ extern "C" {
  * LLL_PICARD: the drift of Eq. (bdrift), evaluated at the Picard iterate
  * Z^(1) of Eq. (Picard-2) (Section 3.1).  LLL_FROZEN: L^0 = exp(Z^(1)), the
  * frozen-drift approximation (Section 1, Section 3.2).  LLL_MLP: the full
- * scheme with the jump compensator replaced by a trained network. */
-typedef enum { LLL_FULL = 0, LLL_PICARD = 1, LLL_MLP = 2, LLL_FROZEN = 3 } lll_scheme;
+ * scheme with the jump compensator replaced by a trained network.
+ * LLL_EXPAND1 / LLL_EXPAND2: the full scheme with the compensator replaced by
+ * its first / second order drift expansion, Eq. (drifta) / Eq. (drifta2)
+ * (Section 3.3), written with the NIG jump cumulant in closed form (no
+ * nodes); NIG driver only, n <= 64 resp. n <= 16 rates (LLL_EUNSUPPORTED
+ * beyond), LLL_EDOMAIN if a needed cumulant argument leaves |beta + u| < alpha. */
+typedef enum {
+    LLL_FULL = 0,
+    LLL_PICARD = 1,
+    LLL_MLP = 2,
+    LLL_FROZEN = 3,
+    LLL_EXPAND1 = 4,
+    LLL_EXPAND2 = 5
+} lll_scheme;
 
 /* Driver H (Section 2, Eq. (canon-LIBOR)).  LLL_DRIVER_NIG: pure-jump NIG
  * (Section 4), drawn as beta V + sqrt(V) Z + mu h with V inverse Gaussian.

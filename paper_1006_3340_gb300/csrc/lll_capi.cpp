@@ -16,6 +16,7 @@ namespace lll {
 int build_nig_rule(double alpha, double beta, double dbar, double a, int Q, double *nodes,
                    double *weights);
 int simulate_mlp(lll_ctx *ctx, uint64_t first_path, uint64_t paths, uint64_t seed);
+int simulate_expand(lll_ctx *ctx, int order, uint64_t first_path, uint64_t paths, uint64_t seed);
 }
 
 using namespace lll;
@@ -65,6 +66,7 @@ void free_all(lll_ctx *c)
     cudaFree(c->d_tab); cudaFree(c->d_row); cudaFree(c->d_Z0); cudaFree(c->d_c0);
     cudaFree(c->d_strikes); cudaFree(c->d_partials); cudaFree(c->d_sums); cudaFree(c->d_state);
     cudaFree(c->d_snap); cudaFree(c->d_C); cudaFree(c->d_cn); cudaFree(c->d_err);
+    cudaFree(c->d_K1); cudaFree(c->d_K2); cudaFree(c->d_K3);
     mlp_free(c->mlp);
     c->mlp = nullptr;
     for (auto &e : c->ev)
@@ -356,6 +358,11 @@ int lll_simulate(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, 
     if (ctx && scheme == LLL_MLP) {
         if (ctx->ns == 0) return fail(ctx, LLL_ESTATE, "lll_set_strikes must come before lll_simulate");
         return simulate_mlp(ctx, first_path, paths, seed);
+    }
+    if (ctx && (scheme == LLL_EXPAND1 || scheme == LLL_EXPAND2)) {
+        if (ctx->ns == 0) return fail(ctx, LLL_ESTATE, "lll_set_strikes must come before lll_simulate");
+        if (paths == 0) return fail(ctx, LLL_EINVAL, "paths must be > 0");
+        return simulate_expand(ctx, scheme == LLL_EXPAND1 ? 1 : 2, first_path, paths, seed);
     }
     LaunchPlan plan;
     int rc = plan_launch(ctx, scheme, first_path, paths, seed, &plan);

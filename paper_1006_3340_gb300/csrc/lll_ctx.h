@@ -42,6 +42,8 @@ struct lll_ctx {
     std::vector<double> lam; // host copy of lambda [S][n]
     lll::MlpState *mlp = nullptr;
     int mlp_kernel = 0;     // LLL_MLP_KERNEL_*
+    float *d_K1 = nullptr, *d_K2 = nullptr, *d_K3 = nullptr; // drift-expansion tables
+    int expand_order = 0;   // order the tables were built for (0: none)
     int *d_err = nullptr;   // error word of kernels with bounded waits
     bool err_pending = false;
     std::string err;

@@ -8,7 +8,7 @@
 
 namespace lll {
 
-enum Scheme { FULL = 0, PICARD = 1, MLP = 2, FROZEN = 3 };
+enum Scheme { FULL = 0, PICARD = 1, MLP = 2, FROZEN = 3, EXPAND1 = 4, EXPAND2 = 5 };
 
 // Largest padded node count the path kernels are compiled for.
 constexpr int kMaxQP = 128;

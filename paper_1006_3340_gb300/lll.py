@@ -18,9 +18,10 @@ from . import build as _build
 
 LLL_OK, LLL_EINVAL, LLL_EDOMAIN, LLL_ECUDA, LLL_ETIMEOUT, LLL_ENOMEM, LLL_ESTATE, LLL_EUNSUPPORTED = \
     0, -1, -2, -3, -4, -5, -6, -7
-LLL_FULL, LLL_PICARD, LLL_MLP, LLL_FROZEN = 0, 1, 2, 3
+LLL_FULL, LLL_PICARD, LLL_MLP, LLL_FROZEN, LLL_EXPAND1, LLL_EXPAND2 = 0, 1, 2, 3, 4, 5
 LLL_DRIVER_NIG, LLL_DRIVER_BROWNIAN = 0, 1
-SCHEMES = {"full": LLL_FULL, "picard": LLL_PICARD, "mlp": LLL_MLP, "frozen": LLL_FROZEN}
+SCHEMES = {"full": LLL_FULL, "picard": LLL_PICARD, "mlp": LLL_MLP, "frozen": LLL_FROZEN,
+           "expand1": LLL_EXPAND1, "expand2": LLL_EXPAND2}
 
 
 class LLLError(RuntimeError):
