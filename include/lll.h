@@ -296,6 +296,16 @@ int lll_mlp_eval(lll_ctx *ctx, const float *x, const float *y, int rows, float *
 #define LLL_MLP_KERNEL_LAYERED 3
 int lll_mlp_set_kernel(lll_ctx *ctx, int kind);
 
+/* lll_inject -- failure-detection testing: LLL_INJECT_MMA_STALL makes the
+ * next launch of the tensor-memory MLP kernel issue no MMAs, so that its
+ * bounded waits run out (about 2 s): the launch ends by itself, frees its
+ * tensor memory, and the next lll_get_sums / lll_price_caplets returns
+ * LLL_ETIMEOUT; the context stays usable.  No GPU fault is involved.
+ * LLL_INJECT_NONE clears a pending injection. */
+#define LLL_INJECT_NONE 0
+#define LLL_INJECT_MMA_STALL 1
+int lll_inject(lll_ctx *ctx, int what);
+
 /* lll_mlp_save / lll_mlp_load -- flat binary file: magic, (hidden, layers,
  * in_dim, N), the five scales, parameter count, FP32 parameters. */
 int lll_mlp_save(lll_ctx *ctx, const char *path);

@@ -45,6 +45,7 @@ struct lll_ctx {
     float *d_K1 = nullptr, *d_K2 = nullptr, *d_K3 = nullptr; // drift-expansion tables
     int expand_order = 0;   // order the tables were built for (0: none)
     int *d_err = nullptr;   // error word of kernels with bounded waits
+    int inject = 0;         // LLL_INJECT_* for the next launch (failure-detection tests)
     bool err_pending = false;
     std::string err;
 };

@@ -46,6 +46,7 @@ struct MlpArgs {
     const float *Ctab;       // [S][n] compensator at zero weights
     int in_pad;              // padded input width of layer 0
     int *err;                // tensor-core kernel: set non-zero when a wait timed out
+    int stall_mma;           // failure-detection test: the MMA warp issues nothing
 };
 
 // lll_mlp_path.cu

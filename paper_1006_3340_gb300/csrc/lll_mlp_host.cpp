@@ -603,6 +603,8 @@ int simulate_mlp(lll_ctx *ctx, uint64_t first_path, uint64_t paths, uint64_t see
     g.Ctab = ctx->d_C;
     g.in_pad = m->in_pad;
     g.err = ctx->d_err;
+    g.stall_mma = (use_tc && ctx->inject == LLL_INJECT_MMA_STALL) ? 1 : 0;
+    if (use_tc) ctx->inject = LLL_INJECT_NONE; // one launch only
     if (use_tc) {
         MTRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
         ctx->err_pending = true;
@@ -630,6 +632,14 @@ int lll_mlp_set_kernel(lll_ctx *ctx, int kind)
         kind != LLL_MLP_KERNEL_LAYERED)
         return err(ctx, LLL_EINVAL, "unknown MLP kernel");
     ctx->mlp_kernel = kind;
+    return LLL_OK;
+}
+
+int lll_inject(lll_ctx *ctx, int what)
+{
+    if (!ctx) return err(nullptr, LLL_EINVAL, "ctx is NULL");
+    if (what != LLL_INJECT_NONE && what != LLL_INJECT_MMA_STALL) return err(ctx, LLL_EINVAL, "unknown injection");
+    ctx->inject = what;
     return LLL_OK;
 }
 

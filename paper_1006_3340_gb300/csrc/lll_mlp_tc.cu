@@ -17,8 +17,9 @@
 //    thread of a row owns the path: it draws the increments, writes the
 //    feature row, adds the other half's output partial, and makes the Euler
 //    step and the caplet bookkeeping.
-//  * warp 16: allocates 256 TMEM columns (one 128-column accumulator per
-//    tile) and, from one lane, issues the MMAs.  Every layer of every
+//  * warp 16: allocates 512 TMEM columns (two 128-column accumulators per
+//    tile, used alternately so that the next rate's first layer overlaps the
+//    current rate's last epilogue) and, from one lane, issues the MMAs.  Every layer of every
 //    live rate is one 128 x H x K product D = X W^T (kind::f16, BF16 operands
 //    K-major with 128-byte swizzle in shared memory, FP32 D in TMEM), the
 //    tiles taking turns so that one's epilogue overlaps the other's MMA.
@@ -113,15 +114,30 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t par, volatile in
     }
 }
 
-// The same, decided once per warp (lane 0 polls) so that all lanes leave a
-// loop together before any .sync.aligned tcgen05 instruction.
+// The same for a whole warp: every lane tests the barrier and the decisions
+// (done, give up) are warp-uniform, so the warp stays converged and all lanes
+// leave a loop together before any .sync.aligned tcgen05 instruction.
 __device__ __forceinline__ bool warp_wait(uint64_t *b, uint32_t par, volatile int *abort, int *err)
 {
-    int ok = 0;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(b, par, abort, err) ? 1 : 0;
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    __syncwarp(); // orders the other lanes after lane 0's acquire
-    return ok != 0;
+    const uint32_t a = saddr(b);
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t ok;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(ok)
+                     : "r"(a), "r"(par)
+                     : "memory");
+        if (__all_sync(0xffffffffu, ok)) return true;
+        const bool stop = *abort || clock64() - t0 > kWaitBudget;
+        if (__any_sync(0xffffffffu, stop)) {
+            if ((threadIdx.x & 31) == 0 && !*abort) {
+                *abort = 1;
+                atomicOr(err, 1);
+            }
+            return false;
+        }
+    }
 }
 
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -213,12 +229,12 @@ __host__ __device__ inline TcLayout tc_layout(int L, int KB0, int n, int ns)
     t.x = o; o += kGroups * 2 * kTileBytes;       // hidden activations, per tile
     t.bias = o; o += L * kH * 4;                  // b_0 / 2 .. b_{L-1} / 2
     t.wout = o; o += kH * 4;                      // output weights (BF16 values)
-    t.bars = o; o += 10 * 8;                      // mbarriers
+    t.bars = o; o += 12 * 8;                      // mbarriers
     t.misc = o; o += 16;                          // TMEM base, abort word
     t.opart = o; o += kGroups * kRows * 4;        // output partial of the upper column half
     o = (o + 15) & ~15u;
-    t.red = o; o += 2 * (kEpiWarps / 2) * ns * 2 * 8; // per-warp payoff sums, two buffers
-    t.bsum = o; o += n * ns * 4 * 8;              // Kahan accumulators
+    t.red = o; o += kGroups * 2 * 4 * ns * 2 * 8; // per tile: 4 owner warps' payoff sums, two buffers
+    t.bsum = o; o += kGroups * n * ns * 4 * 8;    // per tile: Kahan accumulators
     t.total = o + 1024;                           // slack for aligning the base
     return t;
 }
@@ -235,11 +251,16 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
     float *bias = reinterpret_cast<float *>(sm + lay.bias);
     float *wout = reinterpret_cast<float *>(sm + lay.wout);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + lay.bars);
-    uint64_t *opb = bars + 0;  // [kGroups] operand ready (one arrival per warp of the tile)
-    uint64_t *dnb = bars + 2;  // [kGroups] accumulator ready (commit)
-    uint64_t *outb = bars + 4; // [kGroups] upper-half output partials written (4 arrivals)
-    uint64_t *payb = bars + 6; // payoff partials written (one arrival per path-owning warp)
-    uint64_t *finb = bars + 7; // all MMAs complete (commit)
+    // Operand-ready barriers, one arrival per warp of the tile: feature rows
+    // (first layer) and activations (hidden layers) have separate barriers, so
+    // a warp never arrives twice on one barrier before its phase completed
+    // (every arrival on either is preceded by a wait for the previous product).
+    uint64_t *opu = bars + 0;  // [kGroups] feature row ready
+    uint64_t *opx = bars + 2;  // [kGroups] activations ready
+    uint64_t *dnb = bars + 4;  // [kGroups] accumulator ready (commit)
+    uint64_t *outb = bars + 6; // [kGroups] upper-half output partials written (4 arrivals)
+    uint64_t *payb = bars + 8; // [kGroups] payoff partials of a tile written (its 4 owner warps)
+    uint64_t *finb = bars + 10; // all MMAs complete (commit)
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + lay.misc);
     volatile int *abort = reinterpret_cast<volatile int *>(sm + lay.misc + 4);
     float *opart = reinterpret_cast<float *>(sm + lay.opart);
@@ -262,14 +283,15 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
     }
     for (int e = tid; e < L * kH; e += kThreads) bias[e] = 0.5f * g.wp[g.offb[e / kH] + e % kH]; // half biases
     for (int e = tid; e < kH; e += kThreads) wout[e] = __bfloat162float(g.wh[g.off_wout + e]);
-    for (int e = tid; e < 4 * n * ns; e += kThreads) bsum[e] = 0.0;
+    for (int e = tid; e < kGroups * 4 * n * ns; e += kThreads) bsum[e] = 0.0;
     if (tid == 0) {
         for (int gi = 0; gi < kGroups; ++gi) {
-            mbar_init(&opb[gi], 8);   // the 8 warps of the tile
+            mbar_init(&opu[gi], 8);   // the 8 warps of the tile
+            mbar_init(&opx[gi], 8);
             mbar_init(&dnb[gi], 1);
             mbar_init(&outb[gi], 4);  // the 4 upper-half warps
+            mbar_init(&payb[gi], 4);  // the 4 path-owning warps
         }
-        mbar_init(payb, kEpiWarps / 2);
         mbar_init(finb, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -277,7 +299,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
     fence_async_smem();
     if (warp == kEpiWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
-                     "r"(kGroups * kH));
+                     "r"(kGroups * 2 * kH));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_before();
@@ -288,19 +310,26 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
 
     if (warp == kEpiWarps) {
         // ---------------- MMA issuer ----------------
+        // Job j of a tile (its L products per live rate and step, in layer
+        // order) accumulates into TMEM buffer j & 1 of the tile, so the next
+        // rate's first-layer product can run while the epilogue still reads
+        // the current rate's last layer.  The tiles are served in turn.
         if (lane == 0) {
-            uint32_t ph[kGroups] = {0, 0};
-            bool ok = true;
+            uint32_t phu[kGroups] = {0, 0}, phx[kGroups] = {0, 0};
+            uint64_t job = 0;
+            bool ok = !g.stall_mma; // stalled: nothing is issued, the epilogue's waits run out
             for (uint64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
                 for (int k = 0; ok && k < S; ++k) {
                     const int live = n - (k / s + 1) + 1;
                     for (int r = 0; ok && r < live; ++r) {
-                        for (int l = 0; ok && l < L; ++l) {
+                        for (int l = 0; ok && l < L; ++l, ++job) {
                             for (int gi = 0; gi < kGroups; ++gi) {
-                                if (!mbar_wait(&opb[gi], ph[gi], abort, g.err)) { ok = false; break; }
-                                ph[gi] ^= 1;
+                                uint64_t *ob = l == 0 ? &opu[gi] : &opx[gi];
+                                uint32_t &ph = l == 0 ? phu[gi] : phx[gi];
+                                if (!mbar_wait(ob, ph, abort, g.err)) { ok = false; break; }
+                                ph ^= 1;
                                 tc_after();
-                                const uint32_t d = tmem + gi * kH;
+                                const uint32_t d = tmem + gi * 2 * kH + (uint32_t)(job & 1) * kH;
                                 const uint32_t abase = sbase + (l == 0 ? lay.u + gi * KB0 * kTileBytes
                                                                        : lay.x + gi * 2 * kTileBytes);
                                 const uint32_t bbase = sbase + (l == 0 ? lay.w0 : lay.w + (l - 1) * 2 * kTileBytes);
@@ -330,13 +359,15 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
         const int T = kGroups * kRows;           // paths per CTA tile
         const int col = gi * kRows + row;        // column of this path in the state slot
         const bool owner = hf == 0;
-        const int owarp = gi * 4 + q4;           // index of a path-owning warp
+        double *tred = red + (size_t)gi * 2 * 4 * ns * 2;   // this tile's warp sums
+        double *tsum = bsum + (size_t)gi * 4 * n * ns;       // this tile's accumulators
         unsigned char *xptr = sm + lay.x + gi * 2 * kTileBytes;
-        const uint32_t dcol = tmem + ((uint32_t)(q4 * 32) << 16) + gi * kH + hf * 64;
+        const uint32_t dcol = tmem + ((uint32_t)(q4 * 32) << 16) + gi * 2 * kH + hf * 64; // + buffer * kH
         float *st = a.state + (size_t)blockIdx.x * n * T + col;
         const float h = a.h, delta = a.delta;
         const float b_out = g.wp[g.off_bout];
         uint32_t phd = 0, pho = 0, php = 0;
+        uint64_t job = 0; // this tile's product count: TMEM buffer = job & 1
         int mcount = 0;
         bool ok = true;
         for (uint64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
@@ -380,6 +411,16 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                     lam_c = a.row[(size_t)k * n + (n - 1)].x;
                     C_c = g.Ctab[(size_t)k * n + (n - 1)];
                 }
+                // columns 0..7 of rate i's feature row: t, i, lambda_i, u_0 = 0, u_1 .. u_4
+                unsigned char *urow0 = sm + lay.u + gi * KB0 * kTileBytes + chunk_off(row, 0, 0);
+                if (owner)
+                    *reinterpret_cast<uint4 *>(urow0) =
+                        make_uint4(pack2(xt, (float)n * g.sc.i_scale), pack2(lam_c * g.sc.lam_scale, 0.0f), u14[0],
+                                   u14[1]);
+                fence_async_smem();
+                tc_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&opu[gi]);
                 for (int i = n; ok && i >= imin; --i) {
                     const size_t rowk = (size_t)k * n + (i - 1);
                     float *sp = st + (size_t)(i - 1) * T;
@@ -390,26 +431,21 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                             lam_n = a.row[rowk - 1].x;
                             C_n = g.Ctab[rowk - 1];
                         }
-                        // columns 0..7: t, i, lambda_i, u_0 = 0, u_1 .. u_4
-                        *reinterpret_cast<uint4 *>(sm + lay.u + gi * KB0 * kTileBytes + chunk_off(row, 0, 0)) =
-                            make_uint4(pack2(xt, (float)i * g.sc.i_scale), pack2(lam_c * g.sc.lam_scale, 0.0f),
-                                       u14[0], u14[1]);
                     }
-                    fence_async_smem();
-                    tc_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&opb[gi]);
                     float o4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
                     for (int l = 0; l < L; ++l) {
-                        if (!warp_wait(&dnb[gi], phd, abort, g.err)) { ok = false; break; }
+                        if (!ok) continue;
+                        if (!warp_wait(&dnb[gi], phd, abort, g.err)) { ok = false; continue; }
                         phd ^= 1;
                         tc_after();
+                        const uint32_t dbuf = dcol + (uint32_t)(job & 1) * kH;
+                        ++job;
                         const float *hbl = bias + l * kH + hf * 64;
                         uint32_t ra[32], rb[32];
-                        tmem_ld32(dcol, ra);
+                        tmem_ld32(dbuf, ra);
                         tmem_wait32(ra);
-                        tmem_ld32(dcol + 32, rb);
+                        tmem_ld32(dbuf + 32, rb);
 #pragma unroll
                         for (int cc = 0; cc < 2; ++cc) {
                             const uint32_t *cur = cc ? rb : ra;
@@ -439,7 +475,20 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                             fence_async_smem();
                             tc_before();
                             __syncwarp();
-                            if (lane == 0) mbar_arrive(&opb[gi]);
+                            if (lane == 0) mbar_arrive(&opx[gi]);
+                        }
+                        if (l == L - 2 && i > imin) {
+                            // the next rate's feature row (same t_k, so only columns 0..7
+                            // change): its first-layer product runs during this rate's last
+                            // epilogue, into the other TMEM buffer
+                            if (owner)
+                                *reinterpret_cast<uint4 *>(urow0) =
+                                    make_uint4(pack2(xt, (float)(i - 1) * g.sc.i_scale),
+                                               pack2(lam_n * g.sc.lam_scale, 0.0f), u14[0], u14[1]);
+                            fence_async_smem();
+                            tc_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&opu[gi]);
                         }
                     }
                     if (!ok) break;
@@ -468,6 +517,9 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                 }
                 if (!ok) break;
                 if (mat && owner) {
+                    // the tile's 4 owner warps reduce their paths; the first of
+                    // them adds the four sums in fixed order (tiles run apart,
+                    // so each has its own barrier and accumulators)
                     const int m = imin, buf = mcount & 1;
                     ++mcount;
                     for (int qs = 0; qs < ns; ++qs) {
@@ -476,25 +528,24 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                         const double s1 = warp_sum(pay);
                         const double s2 = warp_sum(pay * pay);
                         if (lane == 0) {
-                            red[(((size_t)buf * (kEpiWarps / 2) + owarp) * ns + qs) * 2 + 0] = s1;
-                            red[(((size_t)buf * (kEpiWarps / 2) + owarp) * ns + qs) * 2 + 1] = s2;
+                            tred[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 0] = s1;
+                            tred[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 1] = s2;
                         }
                     }
-                    if (lane == 0) mbar_arrive(payb);
-                    if (warp == 0) {
-                        // all path-owning warps have written this maturity's sums
-                        if (!warp_wait(payb, php, abort, g.err)) { ok = false; break; }
-                    }
-                    if (tid == 0) {
-                        for (int qs = 0; qs < ns; ++qs) {
-                            double s1 = 0.0, s2 = 0.0;
-                            for (int wv = 0; wv < kEpiWarps / 2; ++wv) {
-                                s1 += red[(((size_t)buf * (kEpiWarps / 2) + wv) * ns + qs) * 2 + 0];
-                                s2 += red[(((size_t)buf * (kEpiWarps / 2) + wv) * ns + qs) * 2 + 1];
+                    if (lane == 0) mbar_arrive(&payb[gi]);
+                    if (q4 == 0) {
+                        if (!warp_wait(&payb[gi], php, abort, g.err)) { ok = false; break; }
+                        if (lane == 0) {
+                            for (int qs = 0; qs < ns; ++qs) {
+                                double s1 = 0.0, s2 = 0.0;
+                                for (int wv = 0; wv < 4; ++wv) {
+                                    s1 += tred[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 0];
+                                    s2 += tred[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 1];
+                                }
+                                double *acc = tsum + 4 * ((size_t)(m - 1) * ns + qs);
+                                kahan_add(acc + 0, acc + 1, s1);
+                                kahan_add(acc + 2, acc + 3, s2);
                             }
-                            double *acc = bsum + 4 * ((size_t)(m - 1) * ns + qs);
-                            kahan_add(acc + 0, acc + 1, s1);
-                            kahan_add(acc + 2, acc + 3, s2);
                         }
                     }
                     php ^= 1;
@@ -506,12 +557,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
     __syncthreads();
     if (warp == kEpiWarps) {
         tc_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kGroups * kH));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kGroups * 2 * kH));
     }
     double *out = a.partials + (size_t)blockIdx.x * n * ns * 2;
     for (int e = tid; e < n * ns; e += kThreads) {
-        out[2 * e + 0] = bsum[4 * e + 0];
-        out[2 * e + 1] = bsum[4 * e + 2];
+        out[2 * e + 0] = bsum[4 * e + 0] + bsum[4 * ((size_t)n * ns + e) + 0];
+        out[2 * e + 1] = bsum[4 * e + 2] + bsum[4 * ((size_t)n * ns + e) + 2];
     }
 }
 

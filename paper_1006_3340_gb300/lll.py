@@ -88,6 +88,7 @@ def load():
         "lll_mlp_save": (I, [V, ctypes.c_char_p]),
         "lll_mlp_load": (I, [V, ctypes.c_char_p]),
         "lll_mlp_set_kernel": (I, [V, I]),
+        "lll_inject": (I, [V, I]),
         "lll_batch_init": (I, [ctypes.POINTER(V), I, ctypes.POINTER(lll_instance), V]),
         "lll_batch_set_launch": (I, [V, I, I, I]),
         "lll_batch_use_graph": (I, [V, I]),
@@ -260,6 +261,12 @@ def lll_mlp_load(ctx, path):
 
 
 MLP_KERNELS = {"auto": 0, "warp": 1, "tc": 2, "layered": 3}
+LLL_INJECT_NONE, LLL_INJECT_MMA_STALL = 0, 1
+
+
+def lll_inject(ctx, what):
+    """Failure-detection testing (see include/lll.h)."""
+    _check(load().lll_inject(ctx, int(what)), ctx)
 
 
 def lll_mlp_set_kernel(ctx, kind):

@@ -280,3 +280,26 @@ def test_wide_network_on_long_dated_workload_matches_fp64_scheme(lll):
     err = np.abs(z[mask] - ref["snap"][mask]).max()
     assert err <= tol, (err, tol)
     assert np.abs(p - ref["price"]).max() <= 1e-2 * tol
+
+
+def test_bounded_wait_gives_up_and_context_stays_usable(lll, trained):
+    """Failure detection without a GPU fault: with LLL_INJECT_MMA_STALL the
+    MMA warp issues nothing, the epilogue's bounded waits run out, the launch
+    ends by itself and the results read back as LLL_ETIMEOUT (-4); the next
+    simulation on the same context is exact again."""
+    wl, x, W, sim, loss = trained
+    cnt = 2048
+    try:
+        lll.lll_mlp_set_kernel(sim.ctx, "tc")
+        sim.simulate("mlp", paths=cnt)
+        ref, _ = sim.prices()
+        lll.lll_inject(sim.ctx, lll.LLL_INJECT_MMA_STALL)
+        sim.simulate("mlp", paths=cnt)
+        with pytest.raises(lll.LLLError) as e:
+            sim.prices()
+        assert e.value.code == -4
+        sim.simulate("mlp", paths=cnt)
+        again, _ = sim.prices()
+    finally:
+        lll.lll_mlp_set_kernel(sim.ctx, "auto")
+    assert np.array_equal(ref, again)
