@@ -99,6 +99,21 @@ int lll_init(lll_ctx **out, int N, double tenor_delta, const double *L0, int ste
              const double *lambda, int driver, lll_nig nig, int Q, const double *nodes,
              const double *weights, void *cuda_stream);
 
+/* lll_set_product -- the payoff recorded at every T_m (m = 1..n) for the
+ * strikes of lll_set_strikes; takes effect at the next simulation.
+ *   LLL_PRODUCT_CAPLET (0, default): the caplet of Eq. (caplet) on L(T_m, T_m).
+ *   LLL_PRODUCT_SWAPTION (1): the co-terminal payer swaption expiring at T_m
+ *     on the swap over [T_m, T_N] (fixed rate K against L, both legs paying at
+ *     T_{m+1} .. T_N), a multi-LIBOR derivative (Section 1): its value at T_m
+ *     is (1 - B(T_m,T_N) - K delta sum_{j>m} B(T_m,T_j))^+, priced under the
+ *     terminal measure as B(0,T_N) E[((1 + delta L_m) P - 1 - K delta S)^+]
+ *     with P = prod_{l>m} (1 + delta L_l(T_m)) and S = sum_{j=m+1}^{N}
+ *     prod_{l>=j} (1 + delta L_l(T_m)) (FP64 on the GPU).  lll_price_caplets
+ *     then returns swaption prices.  The batched launch prices caplets only. */
+#define LLL_PRODUCT_CAPLET 0
+#define LLL_PRODUCT_SWAPTION 1
+int lll_set_product(lll_ctx *ctx, int product);
+
 /* lll_set_strikes -- strikes of the caplets of Eq. (caplet), needed before
  * lll_simulate because payoffs are accumulated on the fly.
  *   n_strikes: 1..64; strikes: [n][n_strikes], row m-1 = caplet fixing at T_m. */

@@ -146,6 +146,7 @@ int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, u
     a.driver = ctx->driver;
     a.h = (float)ctx->h; a.sqrt_h = (float)std::sqrt(ctx->h); a.delta = (float)ctx->delta;
     a.dBN = (float)(ctx->delta * ctx->BN);
+    a.product = ctx->product;
     if (ctx->driver == LLL_DRIVER_NIG) {
         const double m = ctx->nig.delta * ctx->h / ctx->gam;
         const double l = (ctx->nig.delta * ctx->h) * (ctx->nig.delta * ctx->h);
@@ -293,6 +294,15 @@ int lll_init(lll_ctx **out, int N, double tenor_delta, const double *L0, int ste
     if (domain_warn)
         return fail(c, LLL_EDOMAIN,
                     "sum |lambda| >= alpha - |beta|: the compensator uses the measure truncated to the rule");
+    return LLL_OK;
+}
+
+int lll_set_product(lll_ctx *ctx, int product)
+{
+    if (!ctx) return fail(nullptr, LLL_EINVAL, "ctx is NULL");
+    if (product != LLL_PRODUCT_CAPLET && product != LLL_PRODUCT_SWAPTION)
+        return fail(ctx, LLL_EINVAL, "unknown product");
+    ctx->product = product;
     return LLL_OK;
 }
 

@@ -34,6 +34,7 @@ struct lll_ctx {
     float *d_snap = nullptr;
     uint64_t n_snap = 0, snap_stride = 1;
     int ns = 0;
+    int product = 0; // LLL_PRODUCT_*
     bool simulated = false;
     uint64_t last_paths = 0;
     uint64_t last_snap_paths = 0;

@@ -79,4 +79,42 @@ __device__ __forceinline__ float draw_increment(const PathArgs &a, uint64_t p, u
     return fmaf(a.nig_beta, V, fmaf(sqrtf(V), z2, a.nig_muh));
 }
 
+// Payoff quantities of one path at T_m from its log-rates z(i) = log L_i(T_m),
+// i = m..n (z is a callable): L_m, P = prod_{l>m} (1 + delta L_l) and, for
+// swaptions, S = 1 + sum_{j=m+1}^{n} prod_{l>=j} (1 + delta L_l), i.e.
+// B(T_m, T_j) / B(T_m, T_N) summed over the payment dates T_{m+1} .. T_N.
+// Caplets keep P in FP32 (a product of factors near 1, multiplied by a
+// non-negative payoff); swaptions keep P and S in FP64 (each factor formed as
+// 1 + fl32(delta L)), because their payoff subtracts 1 from them.
+template <class ZF>
+__device__ __forceinline__ void maturity_products(const PathArgs &a, int m, ZF z, double &P, double &S, float &Lm)
+{
+    if (a.product == 0) {
+        float Pf = 1.0f;
+        for (int i = a.n; i > m; --i) Pf *= fmaf(a.delta, expf(z(i)), 1.0f);
+        P = (double)Pf;
+        S = 1.0;
+    } else {
+        P = 1.0;
+        S = 1.0;
+        for (int i = a.n; i > m; --i) {
+            P *= 1.0 + (double)(a.delta * expf(z(i)));
+            S += P;
+        }
+    }
+    Lm = expf(z(m));
+}
+
+// Discounted payoff (under the terminal measure, times B(0, T_N)) at T_m for
+// strike K.  Caplet, Eq. (caplet): delta B(0,T_N) prod_{l>m} (1 + delta L_l) (L_m - K)^+.
+// Co-terminal payer swaption on the swap over [T_m, T_N]: its value at T_m is
+// (1 - B(T_m,T_N) - K delta sum_{j>m} B(T_m,T_j))^+, and divided by the
+// numeraire B(T_m, T_N) it is ((1 + delta L_m) P - 1 - K delta S)^+.
+__device__ __forceinline__ double payoff(const PathArgs &a, double P, double S, float Lm, float K)
+{
+    if (a.product == 0) return (double)(a.dBN * (float)P * fmaxf(Lm - K, 0.0f));
+    const double X = (1.0 + (double)(a.delta * Lm)) * P - 1.0 - (double)K * (double)a.delta * S;
+    return X > 0.0 ? (double)a.dBN / (double)a.delta * X : 0.0;
+}
+
 }  // namespace lll

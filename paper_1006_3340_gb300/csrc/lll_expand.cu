@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kT) expand_kernel(const PathArgs a, const floa
     for (int e = tid; e < 4 * n * ns; e += kT) bsum[e] = 0.0;
     float *st = a.state + (size_t)blockIdx.x * n * kT + tid;
     const uint64_t ntiles = (a.paths + kT - 1) / kT;
-    const float h = a.h, delta = a.delta;
+    const float h = a.h;
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint64_t lp = tile * kT + tid;
         const bool active = lp < a.paths;
@@ -82,7 +82,6 @@ __global__ void __launch_bounds__(kT) expand_kernel(const PathArgs a, const floa
                 ws[(size_t)(l - 1) * kT + tid] = L / (1.0f + L);
             }
             __syncthreads();
-            float num = 1.0f, Lm = 0.0f;
             for (int i = n; i >= imin; --i) {
                 const float *r2 = k2 + (size_t)(i - 1) * n;
                 float A = k1[i - 1];
@@ -99,18 +98,17 @@ __global__ void __launch_bounds__(kT) expand_kernel(const PathArgs a, const floa
                 float *sp = st + (size_t)(i - 1) * kT;
                 const float z = sp[0] + fmaf(a.row[(size_t)k * n + (i - 1)].x, dH, -A * h);
                 sp[0] = z;
-                if (mat) {
-                    const float znew = z + a.Z0[i - 1];
-                    if (i > imin) num *= fmaf(delta, expf(znew), 1.0f);
-                    else Lm = expf(znew);
-                    if (sidx != ~0ull) a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = znew;
-                }
+                if (mat && sidx != ~0ull)
+                    a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = z + a.Z0[i - 1];
             }
             if (mat) {
                 const int m = imin;
+                double Pp, Sp;
+                float Lm;
+                maturity_products(a, m, [&](int i) { return st[(size_t)(i - 1) * kT] + a.Z0[i - 1]; }, Pp, Sp, Lm);
                 for (int q = 0; q < ns; ++q) {
                     const float K = a.strikes[(size_t)(m - 1) * ns + q];
-                    const double pay = active ? (double)(a.dBN * num * fmaxf(Lm - K, 0.0f)) : 0.0;
+                    const double pay = active ? payoff(a, Pp, Sp, Lm, K) : 0.0;
                     const double s1 = warp_sum(pay), s2 = warp_sum(pay * pay);
                     if (lane == 0) {
                         red[((size_t)warp * ns + q) * 2 + 0] = s1;

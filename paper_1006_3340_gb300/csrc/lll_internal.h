@@ -32,6 +32,7 @@ struct PathArgs {
     uint32_t key0, key1, inst;
     int driver;           // 0 NIG, 1 Brownian
     float h, sqrt_h, delta, dBN; // dBN = delta * B(0, T_N)
+    int product;          // 0: caplets, 1: co-terminal payer swaptions (see lll_device.cuh)
     // NIG increment over one step: IG(mean m, shape l) mixing variable.
     float ig_m, ig_m2, ig_hl, ig_fl; // m, m^2, m / (2 l), 4 m l
     float nig_beta, nig_muh;         // beta, mu * h

@@ -70,7 +70,6 @@ __global__ void __launch_bounds__(kT) euler_kernel(const PathArgs a, const float
     const bool mat = (k + 1) % s == 0;
     const uint64_t lp = chunk_first + (uint64_t)p;
     const bool active = p < Pc && lp < a.paths;
-    float num = 1.0f, Lm = 0.0f;
     if (p < Pc) {
         uint64_t sidx = ~0ull;
         if (a.snap != nullptr && active && lp % a.snap_stride == 0 && lp / a.snap_stride < a.n_snap)
@@ -83,19 +82,19 @@ __global__ void __launch_bounds__(kT) euler_kernel(const PathArgs a, const float
             float *sp = state + (size_t)(i - 1) * Pc + p;
             const float z = sp[0] + fmaf(a.row[rowk].x, dH, -A * h);
             sp[0] = z;
-            if (mat) {
-                const float znew = z + a.Z0[i - 1];
-                if (i > imin) num *= fmaf(a.delta, expf(znew), 1.0f);
-                else Lm = expf(znew);
-                if (sidx != ~0ull) a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = znew;
-            }
+            if (mat && sidx != ~0ull)
+                a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = z + a.Z0[i - 1];
         }
     }
     if (!mat) return;
     const int m = imin;
+    double Pp = 1.0, Sp = 1.0;
+    float Lm = 0.0f;
+    if (p < Pc)
+        maturity_products(a, m, [&](int i) { return state[(size_t)(i - 1) * Pc + p] + a.Z0[i - 1]; }, Pp, Sp, Lm);
     for (int q = 0; q < ns; ++q) {
         const float K = a.strikes[(size_t)(m - 1) * ns + q];
-        const double pay = active ? (double)(a.dBN * num * fmaxf(Lm - K, 0.0f)) : 0.0;
+        const double pay = active ? payoff(a, Pp, Sp, Lm, K) : 0.0;
         const double s1 = warp_sum(pay), s2 = warp_sum(pay * pay);
         if (lane == 0) {
             red[warp][q][0] = s1;

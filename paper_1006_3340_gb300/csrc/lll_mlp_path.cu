@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) mlp_path_kernel(const PathArgs
 
     float *st = a.state + (size_t)blockIdx.x * n * T + tid;
     const uint64_t ntiles = (a.paths + T - 1) / T;
-    const float h = a.h, delta = a.delta;
+    const float h = a.h;
 
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint64_t lp = tile * (uint64_t)T + tid;
@@ -244,7 +244,6 @@ __global__ void __launch_bounds__(kWarps * 32, 1) mlp_path_kernel(const PathArgs
             }
             __syncwarp();
             // Euler step of this lane's path with A_i = C_i + s_y f
-            float num = 1.0f, Lm = 0.0f;
             for (int i = n; i >= imin; --i) {
                 const size_t row = (size_t)k * n + (i - 1);
                 const float lam = a.row[row].x;
@@ -252,19 +251,17 @@ __global__ void __launch_bounds__(kWarps * 32, 1) mlp_path_kernel(const PathArgs
                 float *sp = st + (size_t)(i - 1) * T;
                 const float z = sp[0] + fmaf(lam, dH, -A * h);
                 sp[0] = z;
-                if (mat) {
-                    const float znew = z + a.Z0[i - 1];
-                    if (i > imin) num *= fmaf(delta, expf(znew), 1.0f);
-                    else Lm = expf(znew);
-                    if (sidx != ~0ull)
-                        a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = znew;
-                }
+                if (mat && sidx != ~0ull)
+                    a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = z + a.Z0[i - 1];
             }
             if (mat) {
                 const int m = imin;
+                double Pp, Sp;
+                float Lm;
+                maturity_products(a, m, [&](int i) { return st[(size_t)(i - 1) * T] + a.Z0[i - 1]; }, Pp, Sp, Lm);
                 for (int q = 0; q < ns; ++q) {
                     const float K = a.strikes[(size_t)(m - 1) * ns + q];
-                    const double pay = active ? (double)(a.dBN * num * fmaxf(Lm - K, 0.0f)) : 0.0;
+                    const double pay = active ? payoff(a, Pp, Sp, Lm, K) : 0.0;
                     const double s1 = warp_sum(pay);
                     const double s2 = warp_sum(pay * pay);
                     if (lane == 0) {

@@ -157,29 +157,24 @@ __device__ __forceinline__ void mma_commit(uint64_t *b)
                  : "memory");
 }
 
-// 32 consecutive FP32 accumulator columns of this thread's TMEM lane: the
-// load is issued by tmem_ld32 and its registers become valid at tmem_wait32,
+// 16 consecutive FP32 accumulator columns of this thread's TMEM lane: the
+// load is issued by tmem_ld16 and its registers become valid at tmem_wait16,
 // which takes them as in/out operands so that no use is scheduled before it.
-#define LLL_R32(r) "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), \
-    "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),           \
-    "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),         \
-    "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+#define LLL_R16(r) "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), \
+    "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
 
-__device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&r)[32])
+__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&r)[16])
 {
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                  : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
                    "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                   "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-                   "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-                   "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                   "=r"(r[14]), "=r"(r[15])
                  : "r"(ta));
 }
 
-__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32])
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16])
 {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" : LLL_R32(r) : : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : LLL_R16(r) : : "memory");
 }
 
 // Bias + SiLU of 8 accumulator values: with z = v + b and hz = z / 2 (from
@@ -364,7 +359,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
         unsigned char *xptr = sm + lay.x + gi * 2 * kTileBytes;
         const uint32_t dcol = tmem + ((uint32_t)(q4 * 32) << 16) + gi * 2 * kH + hf * 64; // + buffer * kH
         float *st = a.state + (size_t)blockIdx.x * n * T + col;
-        const float h = a.h, delta = a.delta;
+        const float h = a.h;
         const float b_out = g.wp[g.off_bout];
         uint32_t phd = 0, pho = 0, php = 0;
         uint64_t job = 0; // this tile's product count: TMEM buffer = job & 1
@@ -405,7 +400,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                     u14[0] = pack2(f[0], f[1]);
                     u14[1] = pack2(f[2], f[3]);
                 }
-                float num = 1.0f, Lm = 0.0f;
                 float lam_c = 0.0f, C_c = 0.0f;
                 if (owner) {
                     lam_c = a.row[(size_t)k * n + (n - 1)].x;
@@ -442,25 +436,26 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                         const uint32_t dbuf = dcol + (uint32_t)(job & 1) * kH;
                         ++job;
                         const float *hbl = bias + l * kH + hf * 64;
-                        uint32_t ra[32], rb[32];
-                        tmem_ld32(dbuf, ra);
-                        tmem_wait32(ra);
-                        tmem_ld32(dbuf + 32, rb);
+                        uint32_t ra[16], rb[16];
+                        tmem_ld16(dbuf, ra);
+                        tmem_wait16(ra);
 #pragma unroll
-                        for (int cc = 0; cc < 2; ++cc) {
-                            const uint32_t *cur = cc ? rb : ra;
-                            if (cc == 1) tmem_wait32(rb);
+                        for (int cc = 0; cc < 4; ++cc) {
+                            // columns 64 hf + 16 cc .. +15; the next chunk loads meanwhile
+                            uint32_t(&cur)[16] = (cc & 1) ? rb : ra;
+                            uint32_t(&nxt)[16] = (cc & 1) ? ra : rb;
+                            if (cc < 3) tmem_ld16(dbuf + (cc + 1) * 16, nxt);
 #pragma unroll
-                            for (int qd = 0; qd < 4; ++qd) {
+                            for (int qd = 0; qd < 2; ++qd) {
                                 float sv[8];
-                                silu8(cur + qd * 8, hbl + cc * 32 + qd * 8, sv);
+                                silu8(cur + qd * 8, hbl + cc * 16 + qd * 8, sv);
                                 if (l < L - 1) {
-                                    // columns 64 hf + 32 cc + 8 qd .. +7: K block hf, chunk 4 cc + qd
-                                    *reinterpret_cast<uint4 *>(xptr + chunk_off(row, hf, cc * 4 + qd)) =
+                                    // K block hf, 16-byte chunk 2 cc + qd
+                                    *reinterpret_cast<uint4 *>(xptr + chunk_off(row, hf, cc * 2 + qd)) =
                                         make_uint4(pack2(sv[0], sv[1]), pack2(sv[2], sv[3]), pack2(sv[4], sv[5]),
                                                    pack2(sv[6], sv[7]));
                                 } else {
-                                    const float *wo = wout + hf * 64 + cc * 32 + qd * 8;
+                                    const float *wo = wout + hf * 64 + cc * 16 + qd * 8;
 #pragma unroll
                                     for (int e = 0; e < 8; e += 2) {
                                         // BF16 activations (packed round to nearest even), FP32 products
@@ -470,6 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                                     }
                                 }
                             }
+                            if (cc < 3) tmem_wait16(nxt);
                         }
                         if (l < L - 1) {
                             fence_async_smem();
@@ -506,12 +502,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                     const float A = C_c + g.sc.y_scale * (o + b_out);
                     const float z = zold + fmaf(lam_c, dH, -A * h);
                     sp[0] = z;
-                    if (mat) {
-                        const float znew = z + a.Z0[i - 1];
-                        if (i > imin) num *= fmaf(delta, expf(znew), 1.0f);
-                        else Lm = expf(znew);
-                        if (sidx != ~0ull) a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = znew;
-                    }
+                    if (mat && sidx != ~0ull)
+                        a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = z + a.Z0[i - 1];
                     lam_c = lam_n;
                     C_c = C_n;
                 }
@@ -522,9 +514,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                     // so each has its own barrier and accumulators)
                     const int m = imin, buf = mcount & 1;
                     ++mcount;
+                    double Pp, Sp;
+                    float Lm;
+                    maturity_products(a, m, [&](int i) { return st[(size_t)(i - 1) * T] + a.Z0[i - 1]; }, Pp, Sp, Lm);
                     for (int qs = 0; qs < ns; ++qs) {
                         const float K = a.strikes[(size_t)(m - 1) * ns + qs];
-                        const double pay = active ? (double)(a.dBN * num * fmaxf(Lm - K, 0.0f)) : 0.0;
+                        const double pay = active ? payoff(a, Pp, Sp, Lm, K) : 0.0;
                         const double s1 = warp_sum(pay);
                         const double s2 = warp_sum(pay * pay);
                         if (lane == 0) {

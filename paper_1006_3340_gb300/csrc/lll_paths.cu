@@ -150,7 +150,7 @@ __device__ __forceinline__ void run_tile(const PathArgs &a, const Smem &sm, floa
     const int n = a.n, s = a.s, S = a.S, ns = a.ns, CH = a.chunk_rows;
     const size_t rs = (size_t)NST * n * T; // stride between the R paths of a thread
     const uint64_t TP = (uint64_t)T * R;   // paths per tile
-    const float h = a.h, delta = a.delta;
+    const float h = a.h;
     {
         uint64_t lp[R], p[R], sidx[R];
         bool active[R];
@@ -189,9 +189,9 @@ __device__ __forceinline__ void run_tile(const PathArgs &a, const Smem &sm, floa
                     for (int q = 0; q < R; ++q) P[q][j] = cj;
                 }
             }
-            float scont[R], num[R], Lm[R];
+            float scont[R];
 #pragma unroll
-            for (int q = 0; q < R; ++q) { scont[q] = 0.0f; num[q] = 1.0f; Lm[q] = 0.0f; }
+            for (int q = 0; q < R; ++q) scont[q] = 0.0f;
 
             for (int c = 0; c < nch; ++c) {
                 int nk = k, nc = c + 1;
@@ -288,13 +288,8 @@ __device__ __forceinline__ void run_tile(const PathArgs &a, const Smem &sm, floa
                             sp[0] = z;
                             znew = z;
                         }
-                        if (mat) {
-                            znew += a.Z0[i - 1];
-                            if (i > imin) num[q] *= fmaf(delta, expf(znew), 1.0f);
-                            else Lm[q] = expf(znew);
-                            if (sidx[q] != ~0ull)
-                                a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx[q]] = znew;
-                        }
+                        if (mat && sidx[q] != ~0ull)
+                            a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx[q]] = znew + a.Z0[i - 1];
                     }
                 }
                 __syncthreads();
@@ -303,12 +298,22 @@ __device__ __forceinline__ void run_tile(const PathArgs &a, const Smem &sm, floa
 
             if (mat) {
                 const int m = imin;
+                // payoff quantities from the log-rates at T_m (state slot of this thread)
+                double Pp[R], Sp[R];
+                float Lm[R];
+#pragma unroll
+                for (int u = 0; u < R; ++u)
+                    maturity_products(a, m, [&](int i) {
+                        float z = st[u * rs + (size_t)(i - 1) * T];
+                        if (NST == 2) z += st[u * rs + (size_t)(n + i - 1) * T];
+                        return z + a.Z0[i - 1];
+                    }, Pp[u], Sp[u], Lm[u]);
                 for (int q = 0; q < ns; ++q) {
                     const float K = a.strikes[(size_t)(m - 1) * ns + q];
                     double pay = 0.0, pay2 = 0.0;
 #pragma unroll
                     for (int u = 0; u < R; ++u) {
-                        const double v = active[u] ? (double)(a.dBN * num[u] * fmaxf(Lm[u] - K, 0.0f)) : 0.0;
+                        const double v = active[u] ? payoff(a, Pp[u], Sp[u], Lm[u], K) : 0.0;
                         pay += v;
                         pay2 += v * v;
                     }

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kMaxThreads, (QP <= 64 ? 2 : 1)) group_kernel(
     float *st = a.state + (size_t)blockIdx.x * NST * n * T + tid;
     const uint64_t TP = (uint64_t)T;  // one path per lane
     const uint64_t ntiles = (a.paths + TP - 1) / TP;
-    const float h = a.h, delta = a.delta;
+    const float h = a.h;
 
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint64_t lp = tile * TP + tid;
@@ -167,7 +167,6 @@ __global__ void __launch_bounds__(kMaxThreads, (QP <= 64 ? 2 : 1)) group_kernel(
                     P[q][2 * j + 1] = make_float2(cj.z, cj.w);
                 }
             }
-            float num = 1.0f, Lm = 0.0f;
 
             for (int c = 0; c < nch; ++c) {
                 int nk = k, nc = c + 1;
@@ -255,13 +254,8 @@ __global__ void __launch_bounds__(kMaxThreads, (QP <= 64 ? 2 : 1)) group_kernel(
                         sp[0] = z;
                         znew = z;
                     }
-                    if (mat) {
-                        znew += a.Z0[i - 1];
-                        if (i > imin) num *= fmaf(delta, expf(znew), 1.0f);
-                        else Lm = expf(znew);
-                        if (sidx != ~0ull)
-                            a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = znew;
-                    }
+                    if (mat && sidx != ~0ull)
+                        a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = znew + a.Z0[i - 1];
                 }
                 __syncthreads();
                 buf ^= 1;
@@ -269,9 +263,16 @@ __global__ void __launch_bounds__(kMaxThreads, (QP <= 64 ? 2 : 1)) group_kernel(
 
             if (mat) {
                 const int m = imin;
+                double Pp, Sp;
+                float Lm;
+                maturity_products(a, m, [&](int i) {
+                    float z = st[(size_t)(i - 1) * T];
+                    if (NST == 2) z += st[(size_t)(n + i - 1) * T];
+                    return z + a.Z0[i - 1];
+                }, Pp, Sp, Lm);
                 for (int q = 0; q < ns; ++q) {
                     const float K = a.strikes[(size_t)(m - 1) * ns + q];
-                    const double pay = active ? (double)(a.dBN * num * fmaxf(Lm - K, 0.0f)) : 0.0;
+                    const double pay = active ? payoff(a, Pp, Sp, Lm, K) : 0.0;
                     const double s1 = warp_sum(pay);
                     const double s2 = warp_sum(pay * pay);
                     if (lane == 0) {

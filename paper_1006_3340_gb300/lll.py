@@ -70,6 +70,7 @@ def load():
     sigs = {
         "lll_init": (I, [ctypes.POINTER(V), I, ctypes.c_double, _dp, I, _dp, I, lll_nig, I, _dp, _dp, V]),
         "lll_set_strikes": (I, [V, I, _dp]),
+        "lll_set_product": (I, [V, I]),
         "lll_set_snapshots": (I, [V, U64, U64]),
         "lll_simulate": (I, [V, I, U64, U64, U64]),
         "lll_simulate_noalloc": (I, [V, I, U64, U64, U64, V]),
@@ -262,6 +263,12 @@ def lll_mlp_load(ctx, path):
 
 MLP_KERNELS = {"auto": 0, "warp": 1, "tc": 2, "layered": 3}
 LLL_INJECT_NONE, LLL_INJECT_MMA_STALL = 0, 1
+PRODUCTS = {"caplet": 0, "swaption": 1}
+
+
+def lll_set_product(ctx, product):
+    """Payoff at each T_m: "caplet" (default) or "swaption" (co-terminal payer)."""
+    _check(load().lll_set_product(ctx, PRODUCTS[product] if isinstance(product, str) else int(product)), ctx)
 
 
 def lll_inject(ctx, what):
@@ -355,6 +362,9 @@ class LevyLibor:
     def set_strikes(self, strikes):
         lll_set_strikes(self.ctx, strikes)
         self.ns = np.asarray(strikes).shape[1]
+
+    def set_product(self, product):
+        lll_set_product(self.ctx, product)
 
     def simulate(self, scheme="picard", paths=None, first_path=0, seed=None, snapshots=0,
                  snapshot_stride=1):
