@@ -254,21 +254,32 @@ void lll_batch_destroy(lll_batch *b);
  * weights zero (exact, from the FP64 tables).  BF16 weights and activations,
  * FP32 accumulation (tensor cores), FP32 master weights, Adam.  Parameters
  * are one flat FP32 vector: for each hidden layer W (hidden x in) and b,
- * then the output w (hidden) and b (1); lll_mlp_layout gives the offsets. */
+ * then the output w (outputs x hidden) and b (outputs); lll_mlp_layout gives
+ * the offsets.
+ * Vector head (head = 1): one evaluation per (path, Euler step) gives every
+ * rate's compensator: input (t s_t, u_0 .. u_{N-1}), outputs = n padded to 16
+ * (column i - 1 for rate i; rates already fixed are ignored), trained on the
+ * same records with the MSE over their live rates; LLL_MLP then runs layer by
+ * layer (LLL_MLP_KERNEL_LAYERED) at about 1/n of the per-rate cost. */
 typedef struct {
     int hidden;           /* width of every hidden layer: 128 or 256 */
     int layers;           /* hidden layers: 1..4 */
     uint64_t train_paths; /* full-scheme (quadrature) paths simulated to make the data */
     int records_per_path; /* Euler steps recorded per path (1..8), one pair per live rate each */
-    int epochs;           /* passes over the pairs */
+    int epochs;           /* passes over the pairs (head 1: over the records) */
     int batch;            /* rows per Adam step (>= 32) */
     double lr, lr_final;  /* Adam step size, decayed geometrically to lr_final (<= 0: constant) */
     uint64_t seed;
+    int head;             /* 0: one output per (step, rate); 1: vector head */
 } lll_mlp_cfg;
 
 /* lll_mlp_init -- a fresh network (He-uniform weights from `seed`, zero
  * biases) with the context's feature scales; s_y = 1 until trained. */
 int lll_mlp_init(lll_ctx *ctx, int hidden, int layers, uint64_t seed);
+/* The same with the output head chosen (0 per rate, 1 vector). */
+int lll_mlp_init_head(lll_ctx *ctx, int hidden, int layers, int head, uint64_t seed);
+/* lll_mlp_shape -- head (0/1) and output width of the context's network. */
+int lll_mlp_shape(lll_ctx *ctx, int *head, int *outputs);
 
 /* lll_mlp_train -- generate training pairs with the quadrature full scheme on
  * the GPU (paths keyed by cfg->seed, not by pricing seeds), set s_y to the RMS
@@ -286,7 +297,7 @@ int lll_mlp_layout(lll_ctx *ctx, size_t *n_params, int *in_dim, int *in_pad, siz
 int lll_mlp_params(lll_ctx *ctx, int direction, float *params, size_t count, float *scales);
 
 /* lll_mlp_eval -- run the network on host feature rows x[rows][in_dim]:
- * out[rows] (may be NULL).  With targets y[rows]: *loss = mean (f - y)^2, and
+ * out[rows * outputs] (may be NULL).  With targets y[rows]: *loss = mean (f - y)^2, and
  * with grads != NULL its gradient w.r.t. every parameter (flat layout). */
 int lll_mlp_eval(lll_ctx *ctx, const float *x, const float *y, int rows, float *out, float *grads,
                  double *loss);

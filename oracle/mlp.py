@@ -59,6 +59,37 @@ def forward(params, x):
     return h[:, 0], (acts, zs)
 
 
+def forward_vec(params, x):
+    """All output columns [rows, outputs] (vector head)."""
+    h = x
+    for li, (W, b) in enumerate(params):
+        z = h @ W.T + b
+        h = silu(z) if li + 1 < len(params) else z
+    return h
+
+
+def _backprop(params, acts, zs, d):
+    grads = [None] * len(params)
+    for li in range(len(params) - 1, -1, -1):
+        W, b = params[li]
+        grads[li] = (d.T @ acts[li], d.sum(axis=0))
+        if li > 0:
+            d = (d @ W) * silu_grad(zs[li - 1])
+    return grads
+
+
+def loss_and_grads_vec(params, x, y, n):
+    """Vector head: MSE over the first n output columns (the rates; the rest
+    is padding) and its gradients."""
+    _, (acts, zs) = forward(params, x)
+    out = zs[-1]
+    r = out[:, :n] - y[:, :n]
+    loss = float(np.mean(r * r))
+    d = np.zeros_like(out)
+    d[:, :n] = (2.0 / r.size) * r
+    return loss, _backprop(params, acts, zs, d)
+
+
 def loss_and_grads(params, x, y):
     """MSE loss and its gradients w.r.t. every W and b (list like params)."""
     out, (acts, zs) = forward(params, x)
@@ -98,10 +129,11 @@ def bf16_round(a):
     return r.view(np.float32)
 
 
-def params_from_flat(flat, offsets, layers, hidden, in_dim, in_pad):
+def params_from_flat(flat, offsets, layers, hidden, in_dim, in_pad, outputs=1):
     """The network held by the GPU as FP64 (W, b) pairs: hidden-layer and
     output weights as their BF16 values, biases FP32.  ``offsets`` are the
-    flat offsets W_0, b_0, ..., W_{L-1}, b_{L-1}, w_out, b_out."""
+    flat offsets W_0, b_0, ..., W_{L-1}, b_{L-1}, w_out, b_out; the output
+    layer has ``outputs`` rows (1, or n padded for the vector head)."""
     flat = np.asarray(flat, dtype=np.float32)
     params = []
     for l in range(layers):
@@ -110,12 +142,13 @@ def params_from_flat(flat, offsets, layers, hidden, in_dim, in_pad):
         W = W[:, :in_dim] if l == 0 else W
         b = flat[offsets[2 * l + 1]: offsets[2 * l + 1] + hidden]
         params.append((W.astype(np.float64), b.astype(np.float64)))
-    wout = bf16_round(flat[offsets[2 * layers]: offsets[2 * layers] + hidden]).astype(np.float64)[None, :]
-    params.append((wout, flat[offsets[2 * layers + 1]: offsets[2 * layers + 1] + 1].astype(np.float64)))
+    wout = bf16_round(flat[offsets[2 * layers]: offsets[2 * layers] + outputs * hidden]).astype(np.float64)
+    params.append((wout.reshape(outputs, hidden),
+                   flat[offsets[2 * layers + 1]: offsets[2 * layers + 1] + outputs].astype(np.float64)))
     return params
 
 
-def simulate_scheme(model, params, scales, path0=0, npaths=None, strikes=None):
+def simulate_scheme(model, params, scales, path0=0, npaths=None, strikes=None, head=0):
     """Full Euler scheme with the learned compensator, FP64, paths
     path0 .. path0 + npaths - 1 of the model's Philox streams.
 
@@ -125,9 +158,10 @@ def simulate_scheme(model, params, scales, path0=0, npaths=None, strikes=None):
       A_i = C_i(t_k) + s_y f(x_i),  C_i = int (e^{lambda_i x} - 1 - lambda_i x) F(dx)
             (the compensator with every later weight zero, from the oracle's rule),
       log L_i(t_{k+1}) = log L_i(t_k) - A_i h + lambda_i dH_k,
-    all rates of a step using the state at t_k.  Caplet payoffs at each T_m as
-    in Eq. (caplet).  Returns snap[p, m-1, l-1] = log L_l(T_m) (l >= m) and the
-    payoff sums and prices."""
+    all rates of a step using the state at t_k.  Vector head (head = 1): one
+    row per path, x = (t_k s_t, u_0, .., u_n), and A_i = C_i + s_y f(x)_{i-1}.
+    Caplet payoffs at each T_m as in Eq. (caplet).  Returns
+    snap[p, m-1, l-1] = log L_l(T_m) (l >= m) and the payoff sums and prices."""
     from . import analytic
     from . import oracle as ora
 
@@ -154,13 +188,20 @@ def simulate_scheme(model, params, scales, path0=0, npaths=None, strikes=None):
     for k in range(S):
         imin = k // s + 1
         live = np.arange(imin, n + 1)
-        X = np.zeros((npaths, len(live), 3 + wl.N))
-        X[:, :, 0] = k * h * s_t
-        X[:, :, 1] = live * s_i
-        X[:, :, 2] = lam[k, live - 1] * s_lam
-        X[:, :, 4:] = U[:, None, :] * s_u
-        f, _ = forward(params, X.reshape(-1, X.shape[-1]))
-        A = C[k, live - 1][None, :] + s_y * f.reshape(npaths, len(live))
+        if head:
+            X = np.zeros((npaths, 1 + wl.N))
+            X[:, 0] = k * h * s_t
+            X[:, 2:] = U * s_u
+            f = forward_vec(params, X)[:, live - 1]
+        else:
+            X = np.zeros((npaths, len(live), 3 + wl.N))
+            X[:, :, 0] = k * h * s_t
+            X[:, :, 1] = live * s_i
+            X[:, :, 2] = lam[k, live - 1] * s_lam
+            X[:, :, 4:] = U[:, None, :] * s_u
+            f, _ = forward(params, X.reshape(-1, X.shape[-1]))
+            f = f.reshape(npaths, len(live))
+        A = C[k, live - 1][None, :] + s_y * f
         U[:, live - 1] += -A * h + lam[k, live - 1][None, :] * dH[:, k:k + 1]
         if (k + 1) % s == 0:
             m = imin

@@ -187,6 +187,52 @@ __global__ void out_loss(const __nv_bfloat16 *H, int Hdim, const __nv_bfloat16 *
     }
 }
 
+// Vector head: out[r, o] += b[o] for o < O (out from the output GEMM); with
+// targets y (rows x O) and the rows' Euler steps kr, the masked residual
+// over the live rates (o + 1 >= kr / s + 1, o < n): dout = 2 (out - y) / (rows n)
+// (FP32 and BF16), per-block sums of squares and live counts.  One thread per
+// row.
+__global__ void vec_loss(float *out, const float *b, const float *y, const int *kr, int rows, int O, int n, int s,
+                         float *dout, __nv_bfloat16 *douth, double *loss_part, double *cnt_part)
+{
+    __shared__ double red[2][128];
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0, c = 0.0;
+    if (r < rows) {
+        const int imin = y ? kr[r] / s + 1 : 1;
+        const float inv = 2.0f / ((float)rows * (float)n);
+        for (int o = 0; o < O; ++o) {
+            const size_t e = (size_t)r * O + o;
+            const float v = out[e] + b[o];
+            out[e] = v;
+            if (!y) continue;
+            float d = 0.0f;
+            if (o < n && o + 1 >= imin) {
+                const float rr = v - y[e];
+                d = inv * rr;
+                l += (double)rr * rr;
+                c += 1.0;
+            }
+            dout[e] = d;
+            douth[e] = __float2bfloat16(d);
+        }
+    }
+    red[0][threadIdx.x] = l;
+    red[1][threadIdx.x] = c;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + o];
+            red[1][threadIdx.x] += red[1][threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && loss_part) {
+        loss_part[blockIdx.x] = red[0][0];
+        cnt_part[blockIdx.x] = red[1][0];
+    }
+}
+
 // dZ_L[r, c] = dout[r] * w[c] * SiLU'(Z_L[r, c]), FP32 and BF16 copies.
 __global__ void out_backward(const float *dout, const __nv_bfloat16 *w, const float *Z, int rows,
                              int Hdim, float *dZ, __nv_bfloat16 *dZh)
@@ -315,6 +361,14 @@ int mlp_out_loss(const void *H, int Hdim, const void *w, const float *b, const f
     out_loss<<<(rows + 7) / 8, 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(H), Hdim,
                                             static_cast<const __nv_bfloat16 *>(w), b, y, rows, out,
                                             dout, loss_part);
+    return (int)cudaGetLastError();
+}
+
+int mlp_vec_loss(float *out, const float *b, const float *y, const int *kr, int rows, int O, int n, int s,
+                 float *dout, void *douth, double *loss_part, double *cnt_part, cudaStream_t st)
+{
+    vec_loss<<<(rows + 127) / 128, 128, 0, st>>>(out, b, y, kr, rows, O, n, s, dout,
+                                                 static_cast<__nv_bfloat16 *>(douth), loss_part, cnt_part);
     return (int)cudaGetLastError();
 }
 

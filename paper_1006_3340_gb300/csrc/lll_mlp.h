@@ -18,6 +18,8 @@ int mlp_gemm(int ta, int tb, int epi, const void *A, int lda, const void *B, int
 int mlp_splits_used(int K, int splits);
 int mlp_out_loss(const void *H, int Hdim, const void *w, const float *b, const float *y, int rows,
                  float *out, float *dout, double *loss_part, cudaStream_t st);
+int mlp_vec_loss(float *out, const float *b, const float *y, const int *kr, int rows, int O, int n, int s,
+                 float *dout, void *douth, double *loss_part, double *cnt_part, cudaStream_t st);
 int mlp_out_backward(const float *dout, const void *w, const float *Z, int rows, int Hdim, float *dZ,
                      void *dZh, cudaStream_t st);
 int mlp_out_weight_grad(const float *dout, const void *H, int rows, int Hdim, float *gw, float *gb,
@@ -60,9 +62,9 @@ int launch_mlp_path(int layers, int in_pad, int grid, size_t smem, cudaStream_t 
 // lll_mlp_layered.cu (any network: layer-by-layer over the rows of a step)
 int mlp_layered_threads();
 int launch_mlp_features(const PathArgs &a, const MlpScales &sc, int k, int Pc, const float *state, void *X,
-                        int in_pad, cudaStream_t st);
+                        int in_pad, int head, cudaStream_t st);
 int launch_mlp_euler(const PathArgs &a, const float *Ctab, float y_scale, int k, uint64_t chunk_first, int Pc,
-                     float *state, const float *out, double *acc, cudaStream_t st);
+                     float *state, const float *out, int outputs, double *acc, cudaStream_t st);
 int launch_mlp_acc_to_partials(const double *acc, size_t cells, double *partials, cudaStream_t st);
 
 // lll_mlp_tc.cu (tcgen05, accumulators in tensor memory; hidden = 128)
@@ -73,5 +75,11 @@ bool mlp_tc_supported(int hidden, int layers, int in_pad);
 int mlp_tc_occupancy(int layers, int in_pad, size_t smem, int *blocks_per_sm);
 int launch_mlp_tc(int layers, int in_pad, int grid, size_t smem, cudaStream_t st, const PathArgs &a,
                   const MlpArgs &g);
+// vector head (one pass per path and step, 48 output columns)
+size_t mlp_tc_vec_smem(int layers, int in_pad, int n, int ns);
+bool mlp_tc_vec_supported(int hidden, int layers, int in_pad, int outputs, int n);
+int mlp_tc_vec_occupancy(int layers, int in_pad, size_t smem, int *blocks_per_sm);
+int launch_mlp_tc_vec(int layers, int in_pad, int grid, size_t smem, cudaStream_t st, const PathArgs &a,
+                      const MlpArgs &g);
 
 }  // namespace lll

@@ -107,6 +107,29 @@ __global__ void gather_kernel(const float *rec_u, const float *rec_y, const int 
     Y[b] = rec_y[slot * n + (i - 1)] / sc.y_scale;
 }
 
+// Vector head: one training row per recorded (path, step), drawn uniformly:
+// features (t/T_N, u_0 .. u_{N-1}) padded to in_pad, targets y_i / y_scale for
+// every rate (columns i - 1 < O; rates already fixed are masked by the loss
+// through the row's step kr).
+__global__ void gather_vec_kernel(const float *rec_u, const float *rec_y, const int *rec_k, uint64_t nrec, int n,
+                                  int s, double delta, MlpScales sc, int in_pad, int O, int rows, uint32_t key0,
+                                  uint32_t key1, uint32_t step, __nv_bfloat16 *X, float *Y, int *kr)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= rows) return;
+    const int N = n + 1;
+    const uint4 w = philox4x32_10(make_uint4(step, (uint32_t)b, 0x7EC7u, 0u), key0, key1);
+    const uint64_t slot = ((uint64_t)w.x << 32 | w.y) % nrec;
+    const int k = rec_k[slot];
+    __nv_bfloat16 *xr = X + (size_t)b * in_pad;
+    const double h = delta / s;
+    xr[0] = __float2bfloat16((float)(k * h) * sc.t_scale);
+    for (int m = 0; m < N; ++m) xr[1 + m] = __float2bfloat16(rec_u[slot * N + m] * sc.u_scale);
+    for (int c = 1 + N; c < in_pad; ++c) xr[c] = __float2bfloat16(0.0f);
+    for (int o = 0; o < O; ++o) Y[(size_t)b * O + o] = o < n ? rec_y[slot * n + o] / sc.y_scale : 0.0f;
+    kr[b] = k;
+}
+
 // Sum of squares and count of the recorded targets of live rates (per block).
 __global__ void target_moments(const float *rec_y, const int *rec_k, uint64_t nrec, int n, int s,
                                double *part)
@@ -153,6 +176,16 @@ int mlp_gather(const float *rec_u, const float *rec_y, const int *rec_k, uint64_
     gather_kernel<<<(rows + 127) / 128, 128, 0, st>>>(rec_u, rec_y, rec_k, nrec, lam, n, s, delta, sc,
                                                       in_pad, rows, key0, key1, step,
                                                       static_cast<__nv_bfloat16 *>(X), Y);
+    return (int)cudaGetLastError();
+}
+
+int mlp_gather_vec(const float *rec_u, const float *rec_y, const int *rec_k, uint64_t nrec, int n, int s,
+                   double delta, const MlpScales &sc, int in_pad, int O, int rows, uint32_t key0, uint32_t key1,
+                   uint32_t step, void *X, float *Y, int *kr, cudaStream_t st)
+{
+    gather_vec_kernel<<<(rows + 127) / 128, 128, 0, st>>>(rec_u, rec_y, rec_k, nrec, n, s, delta, sc, in_pad, O,
+                                                          rows, key0, key1, step,
+                                                          static_cast<__nv_bfloat16 *>(X), Y, kr);
     return (int)cudaGetLastError();
 }
 

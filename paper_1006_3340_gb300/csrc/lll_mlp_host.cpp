@@ -22,6 +22,9 @@ namespace lll {
 
 int mlp_datagen(int QP, const PathArgs &a, const float *Ctab, int R, uint32_t rec_key, float *state,
                 float *rec_u, float *rec_y, int *rec_k, cudaStream_t st);
+int mlp_gather_vec(const float *rec_u, const float *rec_y, const int *rec_k, uint64_t nrec, int n, int s,
+                   double delta, const MlpScales &sc, int in_pad, int O, int rows, uint32_t key0, uint32_t key1,
+                   uint32_t step, void *X, float *Y, int *kr, cudaStream_t st);
 int mlp_gather(const float *rec_u, const float *rec_y, const int *rec_k, uint64_t nrec, const double *lam,
                int n, int s, double delta, const MlpScales &sc, int in_pad, int rows, uint32_t key0,
                uint32_t key1, uint32_t step, void *X, float *Y, cudaStream_t st);
@@ -30,6 +33,8 @@ int mlp_target_moments(const float *rec_y, const int *rec_k, uint64_t nrec, int 
 
 struct MlpState {
     int hidden = 0, layers = 0, in_dim = 0, in_pad = 0;
+    int head = 0;     // 0: one output per (step, rate) row; 1: all rates' outputs per (step) row
+    int outputs = 1;  // width of the output layer (head 1: n padded to 16)
     MlpScales sc{};
     size_t n_params = 0;
     std::vector<size_t> offW, offb;
@@ -52,11 +57,16 @@ struct MlpState {
     int loss_cap = 0;
     double *d_acc = nullptr;        // layered scheme: per-block Kahan payoff accumulators
     size_t acc_cap = 0;
+    void *d_douth = nullptr;        // head 1: bf16 [cap][outputs] dL/dout
+    int *d_kr = nullptr;            // head 1: Euler step of each training row
+    double *d_cnt = nullptr;        // head 1: per-block counts of live targets
 };
 
 void mlp_free_buffers(MlpState *m)
 {
     cudaFree(m->d_X); cudaFree(m->d_Y); cudaFree(m->d_out); cudaFree(m->d_dout);
+    cudaFree(m->d_douth); cudaFree(m->d_kr); cudaFree(m->d_cnt);
+    m->d_douth = nullptr; m->d_kr = nullptr; m->d_cnt = nullptr;
     for (void *p : m->d_H) cudaFree(p);
     for (float *p : m->d_Z) cudaFree(p);
     m->d_H.clear();
@@ -111,9 +121,9 @@ void layout(MlpState *m)
         o = round8(o + m->hidden);
     }
     m->off_wout = o;
-    o = round8(o + m->hidden);
+    o = round8(o + (size_t)m->outputs * m->hidden);
     m->off_bout = o;
-    o = round8(o + 1);
+    o = round8(o + m->outputs);
     m->n_params = o;
 }
 
@@ -122,10 +132,15 @@ int ensure_rows(lll_ctx *ctx, MlpState *m, int rows)
     if (rows <= m->cap) return LLL_OK;
     mlp_free_buffers(m);
     const size_t H = m->hidden;
+    const size_t O = m->outputs;
     bool ok = cudaMalloc(&m->d_X, 2 * (size_t)rows * m->in_pad) == cudaSuccess &&
-              cudaMalloc(&m->d_Y, 4 * (size_t)rows) == cudaSuccess &&
-              cudaMalloc(&m->d_out, 4 * (size_t)rows) == cudaSuccess &&
-              cudaMalloc(&m->d_dout, 4 * (size_t)rows) == cudaSuccess;
+              cudaMalloc(&m->d_Y, 4 * (size_t)rows * O) == cudaSuccess &&
+              cudaMalloc(&m->d_out, 4 * (size_t)rows * O) == cudaSuccess &&
+              cudaMalloc(&m->d_dout, 4 * (size_t)rows * O) == cudaSuccess;
+    if (ok && m->head)
+        ok = cudaMalloc(&m->d_douth, 2 * (size_t)rows * O) == cudaSuccess &&
+             cudaMalloc((void **)&m->d_kr, 4 * (size_t)rows) == cudaSuccess &&
+             cudaMalloc((void **)&m->d_cnt, sizeof(double) * ((rows + 127) / 128)) == cudaSuccess;
     for (int l = 0; ok && l < m->layers; ++l) {
         void *hp = nullptr;
         float *zp = nullptr;
@@ -173,6 +188,14 @@ int forward(lll_ctx *ctx, MlpState *m, int rows, const float *y)
         Hin = m->d_H[l];
         din = m->hidden;
     }
+    if (m->head) {
+        // out = H W_out^T (FP32), then bias and, with targets, the masked loss
+        MTRY(mlp_gemm(0, 1, 0, Hin, m->hidden, ph + 2 * m->off_wout, m->hidden, rows, m->outputs, m->hidden, 1,
+                      m->d_out, nullptr, nullptr, nullptr, nullptr, st));
+        MTRY(mlp_vec_loss(m->d_out, m->d_p + m->off_bout, y, m->d_kr, rows, m->outputs, ctx->n, ctx->s, m->d_dout,
+                          m->d_douth, y ? m->d_loss : nullptr, m->d_cnt, st));
+        return LLL_OK;
+    }
     MTRY(mlp_out_loss(Hin, m->hidden, ph + 2 * m->off_wout, m->d_p + m->off_bout, y, rows, m->d_out,
                       m->d_dout, y ? m->d_loss : nullptr, st));
     return LLL_OK;
@@ -184,10 +207,24 @@ int backward(lll_ctx *ctx, MlpState *m, int rows)
     cudaStream_t st = ctx->stream;
     const char *ph = static_cast<const char *>(m->d_ph);
     const int H = m->hidden, L = m->layers;
-    MTRY(mlp_out_weight_grad(m->d_dout, m->d_H[L - 1], rows, H, m->d_g + m->off_wout, m->d_g + m->off_bout, st));
-    MTRY(mlp_out_backward(m->d_dout, ph + 2 * m->off_wout, m->d_Z[L - 1], rows, H, m->d_dZ[0], m->d_dZh[0], st));
-    int cur = 0;
     const int splits_req = std::max(1, std::min(64, rows / 256));
+    if (m->head) {
+        const int O = m->outputs;
+        // dW_out = dout^T H_{L-1} (O x H), db_out = column sums, dZ_{L-1} = (dout W_out) * SiLU'(Z_{L-1})
+        const int splits = mlp_splits_used(rows, splits_req);
+        int rc = ensure_split(ctx, m, (size_t)splits * O * H);
+        if (rc != LLL_OK) return rc;
+        MTRY(mlp_gemm(1, 0, 0, m->d_douth, O, m->d_H[L - 1], H, O, H, rows, splits_req, m->d_split, nullptr,
+                      nullptr, nullptr, nullptr, st));
+        MTRY(mlp_reduce_splits(m->d_split, splits, (size_t)O * H, m->d_g + m->off_wout, st));
+        MTRY(mlp_column_sums(m->d_dout, rows, O, m->d_g + m->off_bout, st));
+        MTRY(mlp_gemm(0, 0, 2, m->d_douth, O, ph + 2 * m->off_wout, H, rows, H, O, 1, nullptr, nullptr,
+                      m->d_Z[L - 1], m->d_dZ[0], m->d_dZh[0], st));
+    } else {
+        MTRY(mlp_out_weight_grad(m->d_dout, m->d_H[L - 1], rows, H, m->d_g + m->off_wout, m->d_g + m->off_bout, st));
+        MTRY(mlp_out_backward(m->d_dout, ph + 2 * m->off_wout, m->d_Z[L - 1], rows, H, m->d_dZ[0], m->d_dZh[0], st));
+    }
+    int cur = 0;
     for (int l = L - 1; l >= 0; --l) {
         const int din = l == 0 ? m->in_pad : H;
         const void *Hl = l == 0 ? m->d_X : m->d_H[l - 1];
@@ -211,6 +248,19 @@ int backward(lll_ctx *ctx, MlpState *m, int rows)
 
 double read_loss(lll_ctx *ctx, MlpState *m, int rows, bool *ok)
 {
+    if (m->head) {
+        // mean over the live targets of the batch
+        const int lb = (rows + 127) / 128;
+        std::vector<double> part(lb), cnt(lb);
+        *ok = cudaMemcpyAsync(part.data(), m->d_loss, sizeof(double) * lb, cudaMemcpyDeviceToHost, ctx->stream) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(cnt.data(), m->d_cnt, sizeof(double) * lb, cudaMemcpyDeviceToHost, ctx->stream) ==
+                  cudaSuccess &&
+              cudaStreamSynchronize(ctx->stream) == cudaSuccess;
+        double s = 0.0, c = 0.0;
+        for (int b = 0; b < lb; ++b) { s += part[b]; c += cnt[b]; }
+        return c > 0 ? s / c : 0.0;
+    }
     const int lb = (rows + 7) / 8;
     std::vector<double> part(lb);
     *ok = cudaMemcpyAsync(part.data(), m->d_loss, sizeof(double) * lb, cudaMemcpyDeviceToHost, ctx->stream) ==
@@ -234,7 +284,13 @@ extern "C" {
 
 int lll_mlp_init(lll_ctx *ctx, int hidden, int layers, uint64_t seed)
 {
+    return lll_mlp_init_head(ctx, hidden, layers, 0, seed);
+}
+
+int lll_mlp_init_head(lll_ctx *ctx, int hidden, int layers, int head, uint64_t seed)
+{
     if (!ctx) return err(nullptr, LLL_EINVAL, "ctx is NULL");
+    if (head != 0 && head != 1) return err(ctx, LLL_EINVAL, "head must be 0 (per rate) or 1 (vector)");
     if (ctx->driver != LLL_DRIVER_NIG) return err(ctx, LLL_EINVAL, "the learned compensator needs the NIG driver");
     if ((hidden != 128 && hidden != 256) || layers < 1 || layers > 4)
         return err(ctx, LLL_EINVAL, "hidden must be 128 or 256 and layers 1..4");
@@ -243,7 +299,9 @@ int lll_mlp_init(lll_ctx *ctx, int hidden, int layers, uint64_t seed)
     MlpState *m = new MlpState();
     m->hidden = hidden;
     m->layers = layers;
-    m->in_dim = 3 + ctx->N;
+    m->head = head;
+    m->outputs = head ? (ctx->n + 15) / 16 * 16 : 1;
+    m->in_dim = head ? 1 + ctx->N : 3 + ctx->N;
     m->in_pad = (int)((m->in_dim + 15) / 16 * 16);
     m->sc.t_scale = (float)(1.0 / (ctx->N * ctx->delta));
     m->sc.i_scale = 1.0f / (float)ctx->n;
@@ -264,7 +322,7 @@ int lll_mlp_init(lll_ctx *ctx, int hidden, int layers, uint64_t seed)
     std::mt19937_64 rng(seed);
     for (int l = 0; l <= layers; ++l) {
         const int din = l == 0 ? m->in_dim : hidden;
-        const int rows = l < layers ? hidden : 1;
+        const int rows = l < layers ? hidden : m->outputs;
         const int pitch = l == 0 ? m->in_pad : hidden;
         const size_t off = l < layers ? m->offW[l] : m->off_wout;
         std::uniform_real_distribution<float> U(-std::sqrt(3.0f / din), std::sqrt(3.0f / din));
@@ -311,6 +369,14 @@ int lll_mlp_params(lll_ctx *ctx, int direction, float *params, size_t count, flo
     return LLL_OK;
 }
 
+int lll_mlp_shape(lll_ctx *ctx, int *head, int *outputs)
+{
+    if (!ctx || !ctx->mlp) return err(ctx, LLL_ESTATE, "no network (lll_mlp_init first)");
+    if (head) *head = ctx->mlp->head;
+    if (outputs) *outputs = ctx->mlp->outputs;
+    return LLL_OK;
+}
+
 int lll_mlp_layout(lll_ctx *ctx, size_t *n_params, int *in_dim, int *in_pad, size_t *offsets)
 {
     if (!ctx || !ctx->mlp) return err(ctx, LLL_ESTATE, "no network (lll_mlp_init first)");
@@ -345,7 +411,9 @@ int lll_mlp_eval(lll_ctx *ctx, const float *x, const float *y, int rows, float *
     MTRY(cudaMalloc((void **)&tmp, 4 * xp.size()));
     cudaError_t e = cudaMemcpyAsync(tmp, xp.data(), 4 * xp.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = (cudaError_t)mlp_to_bf16(tmp, xp.size(), m->d_X, st);
-    if (e == cudaSuccess && y) e = cudaMemcpyAsync(m->d_Y, y, 4 * (size_t)rows, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && y)
+        e = cudaMemcpyAsync(m->d_Y, y, 4 * (size_t)rows * m->outputs, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && y && m->head) e = cudaMemsetAsync(m->d_kr, 0, 4 * (size_t)rows, st); // all rates live
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(tmp);
     if (e != cudaSuccess) return cerr(ctx, e, "staging feature rows");
@@ -356,7 +424,7 @@ int lll_mlp_eval(lll_ctx *ctx, const float *x, const float *y, int rows, float *
         if (rc != LLL_OK) return rc;
         MTRY(cudaMemcpyAsync(grads, m->d_g, 4 * m->n_params, cudaMemcpyDeviceToHost, st));
     }
-    if (out) MTRY(cudaMemcpyAsync(out, m->d_out, 4 * (size_t)rows, cudaMemcpyDeviceToHost, st));
+    if (out) MTRY(cudaMemcpyAsync(out, m->d_out, 4 * (size_t)rows * m->outputs, cudaMemcpyDeviceToHost, st));
     MTRY(cudaStreamSynchronize(st));
     if (loss && y) {
         bool ok;
@@ -374,8 +442,10 @@ int lll_mlp_train(lll_ctx *ctx, const lll_mlp_cfg *cfg, double *final_loss)
         cfg->batch < 32 || !(cfg->lr > 0))
         return err(ctx, LLL_EINVAL, "bad training configuration");
     int rc;
-    if (!ctx->mlp || ctx->mlp->hidden != cfg->hidden || ctx->mlp->layers != cfg->layers) {
-        rc = lll_mlp_init(ctx, cfg->hidden, cfg->layers, cfg->seed);
+    if (cfg->head != 0 && cfg->head != 1) return err(ctx, LLL_EINVAL, "head must be 0 or 1");
+    if (!ctx->mlp || ctx->mlp->hidden != cfg->hidden || ctx->mlp->layers != cfg->layers ||
+        ctx->mlp->head != cfg->head) {
+        rc = lll_mlp_init_head(ctx, cfg->hidden, cfg->layers, cfg->head, cfg->seed);
         if (rc != LLL_OK) return rc;
     }
     MlpState *m = ctx->mlp;
@@ -419,16 +489,22 @@ int lll_mlp_train(lll_ctx *ctx, const lll_mlp_cfg *cfg, double *final_loss)
     const int B = cfg->batch;
     rc = ensure_rows(ctx, m, B);
     if (rc != LLL_OK) { cleanup(); return rc; }
-    const uint64_t steps_per_epoch = std::max<uint64_t>(1, (uint64_t)(pairs / B));
+    // an epoch: every recorded pair (head 0) or every record (head 1) once on average
+    const uint64_t steps_per_epoch = std::max<uint64_t>(1, (uint64_t)((m->head ? (double)nrec : pairs) / B));
     const uint64_t total = steps_per_epoch * cfg->epochs;
     const double lr_end = cfg->lr_final > 0 ? cfg->lr_final : cfg->lr;
     double last = 0.0;
     for (uint64_t t = 0; t < total; ++t) {
         const double frac = total > 1 ? (double)t / (total - 1) : 0.0;
         const float lr = (float)(cfg->lr * std::pow(lr_end / cfg->lr, frac));
-        e = (cudaError_t)mlp_gather(rec_u, rec_y, rec_k, nrec, ctx->d_lam, n, ctx->s, ctx->delta, m->sc, m->in_pad,
-                                    B, (uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32), (uint32_t)t, m->d_X,
-                                    m->d_Y, st);
+        if (m->head)
+            e = (cudaError_t)mlp_gather_vec(rec_u, rec_y, rec_k, nrec, n, ctx->s, ctx->delta, m->sc, m->in_pad,
+                                            m->outputs, B, (uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32),
+                                            (uint32_t)t, m->d_X, m->d_Y, m->d_kr, st);
+        else
+            e = (cudaError_t)mlp_gather(rec_u, rec_y, rec_k, nrec, ctx->d_lam, n, ctx->s, ctx->delta, m->sc,
+                                        m->in_pad, B, (uint32_t)cfg->seed, (uint32_t)(cfg->seed >> 32),
+                                        (uint32_t)t, m->d_X, m->d_Y, st);
         if (e != cudaSuccess) { cleanup(); return cerr(ctx, e, "gather"); }
         rc = forward(ctx, m, B, m->d_Y);
         if (rc == LLL_OK) rc = backward(ctx, m, B);
@@ -465,12 +541,14 @@ int simulate_mlp_layered(lll_ctx *ctx, MlpState *m, uint64_t first_path, uint64_
     if (rc != LLL_OK) return rc;
     const int n = ctx->n, s = ctx->s, S = ctx->S, ns = ctx->ns;
     const int T = mlp_layered_threads();
-    // chunk of paths: at most 2^20 rows per step, a multiple of the block size
+    // chunk of paths: at most 2^20 rows per step (one per path and live rate,
+    // or one per path for the vector head), a multiple of the block size
     const uint64_t rows_cap = 1u << 20;
-    uint64_t Pc = std::max<uint64_t>(T, (rows_cap / (uint64_t)n) / T * T);
+    const uint64_t rows_per_path = m->head ? 1 : (uint64_t)n;
+    uint64_t Pc = std::max<uint64_t>(T, (rows_cap / rows_per_path) / T * T);
     Pc = std::min<uint64_t>(Pc, (paths + T - 1) / T * T);
     const int grid = (int)(Pc / T);
-    rc = ensure_rows(ctx, m, (int)(Pc * n));
+    rc = ensure_rows(ctx, m, (int)(Pc * rows_per_path));
     if (rc != LLL_OK) return rc;
     const size_t state_need = (size_t)n * Pc;
     if (state_need > ctx->state_cap) {
@@ -513,10 +591,11 @@ int simulate_mlp_layered(lll_ctx *ctx, MlpState *m, uint64_t first_path, uint64_
         MTRY(cudaMemsetAsync(ctx->d_state, 0, 4 * state_need, st));
         for (int k = 0; k < S; ++k) {
             const int live = n - (k / s + 1) + 1;
-            MTRY(launch_mlp_features(a, m->sc, k, (int)Pc, ctx->d_state, m->d_X, m->in_pad, st));
-            rc = forward(ctx, m, (int)(Pc * live), nullptr);
+            MTRY(launch_mlp_features(a, m->sc, k, (int)Pc, ctx->d_state, m->d_X, m->in_pad, m->head, st));
+            rc = forward(ctx, m, (int)(Pc * (m->head ? 1 : live)), nullptr);
             if (rc != LLL_OK) return rc;
-            MTRY(launch_mlp_euler(a, ctx->d_C, m->sc.y_scale, k, c0, (int)Pc, ctx->d_state, m->d_out, m->d_acc, st));
+            MTRY(launch_mlp_euler(a, ctx->d_C, m->sc.y_scale, k, c0, (int)Pc, ctx->d_state, m->d_out,
+                                  m->head ? m->outputs : 0, m->d_acc, st));
         }
     }
     MTRY(cudaEventRecord(ctx->ev[1], st));
@@ -535,8 +614,20 @@ int simulate_mlp(lll_ctx *ctx, uint64_t first_path, uint64_t paths, uint64_t see
 {
     MlpState *m = ctx->mlp;
     if (!m || !m->trained) return err(ctx, LLL_ESTATE, "LLL_MLP needs lll_mlp_train or lll_mlp_load first");
-    const size_t smem_tc = mlp_tc_smem(m->layers, m->in_pad, ctx->n, ctx->ns);
-    const bool tc_ok = mlp_tc_supported(m->hidden, m->layers, m->in_pad) && smem_tc <= 227 * 1024;
+    bool vec_tc = false;
+    if (m->head) {
+        vec_tc = mlp_tc_vec_supported(m->hidden, m->layers, m->in_pad, m->outputs, ctx->n) &&
+                 mlp_tc_vec_smem(m->layers, m->in_pad, ctx->n, ctx->ns) <= 227 * 1024;
+        if (ctx->mlp_kernel == LLL_MLP_KERNEL_WARP)
+            return err(ctx, LLL_EUNSUPPORTED, "the mma.sync kernel has no vector head");
+        if (ctx->mlp_kernel == LLL_MLP_KERNEL_TC && !vec_tc)
+            return err(ctx, LLL_EUNSUPPORTED, "the tcgen05 vector-head kernel does not support this network");
+        if (ctx->mlp_kernel == LLL_MLP_KERNEL_LAYERED || !vec_tc)
+            return simulate_mlp_layered(ctx, m, first_path, paths, seed);
+    }
+    const size_t smem_tc = vec_tc ? mlp_tc_vec_smem(m->layers, m->in_pad, ctx->n, ctx->ns)
+                                  : mlp_tc_smem(m->layers, m->in_pad, ctx->n, ctx->ns);
+    const bool tc_ok = vec_tc || (mlp_tc_supported(m->hidden, m->layers, m->in_pad) && smem_tc <= 227 * 1024);
     const bool warp_ok = mlp_path_supported(m->hidden, m->layers, m->in_pad) &&
                          mlp_path_smem(m->layers, m->in_pad, ctx->n, ctx->ns) <= 227 * 1024;
     bool use_tc;
@@ -556,7 +647,8 @@ int simulate_mlp(lll_ctx *ctx, uint64_t first_path, uint64_t paths, uint64_t see
     if (rc != LLL_OK) return rc;
     const size_t smem = use_tc ? smem_tc : mlp_path_smem(m->layers, m->in_pad, ctx->n, ctx->ns);
     int occ = 0;
-    if (use_tc) MTRY(mlp_tc_occupancy(m->layers, m->in_pad, smem, &occ));
+    if (vec_tc) MTRY(mlp_tc_vec_occupancy(m->layers, m->in_pad, smem, &occ));
+    else if (use_tc) MTRY(mlp_tc_occupancy(m->layers, m->in_pad, smem, &occ));
     else MTRY(mlp_path_occupancy(m->layers, m->in_pad, smem, &occ));
     if (occ < 1) return err(ctx, LLL_EUNSUPPORTED, "MLP kernel does not fit on an SM");
     if (use_tc && !ctx->d_err) {
@@ -610,7 +702,8 @@ int simulate_mlp(lll_ctx *ctx, uint64_t first_path, uint64_t paths, uint64_t see
         ctx->err_pending = true;
     }
     MTRY(cudaEventRecord(ctx->ev[0], ctx->stream));
-    if (use_tc) MTRY(launch_mlp_tc(m->layers, m->in_pad, grid, smem, ctx->stream, a, g));
+    if (vec_tc) MTRY(launch_mlp_tc_vec(m->layers, m->in_pad, grid, smem, ctx->stream, a, g));
+    else if (use_tc) MTRY(launch_mlp_tc(m->layers, m->in_pad, grid, smem, ctx->stream, a, g));
     else MTRY(launch_mlp_path(m->layers, m->in_pad, grid, smem, ctx->stream, a, g));
     MTRY(cudaEventRecord(ctx->ev[1], ctx->stream));
     MTRY(launch_finalize(ctx->d_partials, grid, (int)nout, ctx->d_sums, ctx->stream));
@@ -683,7 +776,8 @@ int lll_mlp_load(lll_ctx *ctx, const char *path)
     std::fclose(f);
     if (!ok) return err(ctx, LLL_EINVAL, "not a network file");
     if (hdr[3] != ctx->N) return err(ctx, LLL_EINVAL, "network was trained for another tenor count");
-    int rc = lll_mlp_init(ctx, hdr[0], hdr[1], 0);
+    if (hdr[2] != 3 + ctx->N && hdr[2] != 1 + ctx->N) return err(ctx, LLL_EINVAL, "unknown input width");
+    int rc = lll_mlp_init_head(ctx, hdr[0], hdr[1], hdr[2] == 1 + ctx->N ? 1 : 0, 0);
     if (rc != LLL_OK) return rc;
     return lll_mlp_params(ctx, 1, p.data(), p.size(), sc);
 }

@@ -1,7 +1,9 @@
 // lll_mlp_layered.cu -- the learned-compensator scheme (LLL_MLP) for networks
-// the fused kernels cannot hold (hidden width 256, wide inputs): the network
-// runs layer by layer over all (path, live rate) rows of a step with the
-// training GEMMs, between two small kernels of this file.
+// the fused kernels cannot hold (hidden width 256, wide inputs, the vector
+// head): the network runs layer by layer over all rows of a step with the
+// training GEMMs, between two small kernels of this file.  A row is one
+// (path, live rate), or one path for the vector head, whose output layer gives
+// every rate's compensator at once.
 //
 // Per Euler step k of Eq. (log-LIB-SDE-2), for a chunk of paths:
 //  feat_kernel   one BF16 feature row x_i = (t s_t, i s_i, lambda_i s_lam,
@@ -24,6 +26,23 @@ namespace lll {
 namespace {
 
 constexpr int kT = 256; // threads per block of both kernels
+
+// Vector head: one row per path, (t s_t, u_0 .. u_{N-1}).
+__global__ void feat_vec_kernel(const PathArgs a, MlpScales sc, int k, int Pc, const float *state,
+                                __nv_bfloat16 *X, int in_pad)
+{
+    const int n = a.n;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= Pc) return;
+    __nv_bfloat16 *x = X + (size_t)p * in_pad;
+    // columns: 0 t, 1 u_0 = 0, 1 + m  u_m (m = 1..n), then zeros
+    x[0] = __float2bfloat16((float)k * a.h * sc.t_scale);
+    x[1] = __float2bfloat16(0.0f);
+    for (int c = 2; c < in_pad; ++c) {
+        const int m = c - 1;
+        x[c] = __float2bfloat16(m <= n ? state[(size_t)(m - 1) * Pc + p] * sc.u_scale : 0.0f);
+    }
+}
 
 __global__ void feat_kernel(const PathArgs a, MlpScales sc, int k, int Pc, const float *state,
                             __nv_bfloat16 *X, int in_pad)
@@ -60,9 +79,11 @@ __device__ __forceinline__ void kahan_add(double *s, double *c, double x)
     *s = t;
 }
 
+// out: the network outputs of this step, row p * live + (i - imin) (one per
+// path and live rate), or, for the vector head (outputs > 0), row p column i - 1.
 __global__ void __launch_bounds__(kT) euler_kernel(const PathArgs a, const float *Ctab, float y_scale, int k,
                                                     uint64_t chunk_first, int Pc, float *state,
-                                                    const float *out, double *acc)
+                                                    const float *out, int outputs, double *acc)
 {
     __shared__ double red[kT / 32][64][2];
     const int n = a.n, s = a.s, ns = a.ns, imin = k / s + 1, live = n - imin + 1;
@@ -78,7 +99,8 @@ __global__ void __launch_bounds__(kT) euler_kernel(const PathArgs a, const float
         const float h = a.h;
         for (int i = n; i >= imin; --i) {
             const size_t rowk = (size_t)k * n + (i - 1);
-            const float A = Ctab[rowk] + y_scale * out[(size_t)p * live + (i - imin)];
+            const size_t oi = outputs > 0 ? (size_t)p * outputs + (i - 1) : (size_t)p * live + (i - imin);
+            const float A = Ctab[rowk] + y_scale * out[oi];
             float *sp = state + (size_t)(i - 1) * Pc + p;
             const float z = sp[0] + fmaf(a.row[rowk].x, dH, -A * h);
             sp[0] = z;
@@ -127,8 +149,13 @@ __global__ void acc_to_partials(const double *acc, size_t cells, double *partial
 int mlp_layered_threads() { return kT; }
 
 int launch_mlp_features(const PathArgs &a, const MlpScales &sc, int k, int Pc, const float *state, void *X,
-                        int in_pad, cudaStream_t st)
+                        int in_pad, int head, cudaStream_t st)
 {
+    if (head) {
+        feat_vec_kernel<<<(Pc + kT - 1) / kT, kT, 0, st>>>(a, sc, k, Pc, state, static_cast<__nv_bfloat16 *>(X),
+                                                           in_pad);
+        return (int)cudaGetLastError();
+    }
     const int live = a.n - (k / a.s + 1) + 1;
     const size_t rows = (size_t)Pc * live;
     feat_kernel<<<(unsigned)((rows + kT - 1) / kT), kT, 0, st>>>(a, sc, k, Pc, state,
@@ -137,10 +164,10 @@ int launch_mlp_features(const PathArgs &a, const MlpScales &sc, int k, int Pc, c
 }
 
 int launch_mlp_euler(const PathArgs &a, const float *Ctab, float y_scale, int k, uint64_t chunk_first, int Pc,
-                     float *state, const float *out, double *acc, cudaStream_t st)
+                     float *state, const float *out, int outputs, double *acc, cudaStream_t st)
 {
     if (a.ns > 64) return (int)cudaErrorInvalidValue;
-    euler_kernel<<<(Pc + kT - 1) / kT, kT, 0, st>>>(a, Ctab, y_scale, k, chunk_first, Pc, state, out, acc);
+    euler_kernel<<<(Pc + kT - 1) / kT, kT, 0, st>>>(a, Ctab, y_scale, k, chunk_first, Pc, state, out, outputs, acc);
     return (int)cudaGetLastError();
 }
 

@@ -57,6 +57,12 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t a)
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
+// Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_n(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
 // Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = kH.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH >> 3) << 17) |
                             ((uint32_t)(kRows >> 4) << 24);
@@ -149,6 +155,13 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, u
     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
                  "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_bf16_id(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t *b)
@@ -561,6 +574,311 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Vector head: one network pass per (path, Euler step) gives every rate's
+// compensator (output layer N = kOut columns, column i - 1 for rate i).  The
+// CTA layout is the per-rate kernel's (two tiles of 128 paths, two threads per
+// row, one MMA lane); per step a tile runs L hidden products and one output
+// product, then the row's owner applies all live rates' drifts.
+// ---------------------------------------------------------------------------
+constexpr int kOut = 48;                       // output columns (n <= 48)
+constexpr int kOutBlock = kOut * 128;          // one 64-wide K block of W_out (48 rows)
+
+struct TcVecLayout {
+    uint32_t w0, w, wo, u, x, bias, bout, bars, misc, opart, red, bsum, total;
+};
+
+__host__ __device__ inline TcVecLayout tc_vec_layout(int L, int KB0, int n, int ns)
+{
+    TcVecLayout t;
+    uint32_t o = 0;
+    t.w0 = o; o += KB0 * kTileBytes;             // W_0: H rows x 64 KB0 columns
+    t.w = o; o += (L - 1) * 2 * kTileBytes;       // W_1 .. W_{L-1}
+    t.wo = o; o += 2 * kOutBlock;                 // W_out: 48 rows x 128 columns
+    o = (o + 1023) & ~1023u;
+    t.u = o; o += kGroups * KB0 * kTileBytes;     // feature rows, per tile
+    t.x = o; o += kGroups * 2 * kTileBytes;       // hidden activations, per tile
+    t.bias = o; o += L * kH * 4;                  // b_0 / 2 .. b_{L-1} / 2
+    t.bout = o; o += kOut * 4;                    // output biases
+    t.bars = o; o += 12 * 8;
+    t.misc = o; o += 16;
+    t.opart = o; o += 16;                         // (unused by the vector head)
+    o = (o + 15) & ~15u;
+    t.red = o; o += kGroups * 2 * 4 * ns * 2 * 8;
+    t.bsum = o; o += kGroups * n * ns * 4 * 8;
+    t.total = o + 1024;
+    return t;
+}
+
+template <int L, int KB0>
+__global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs a, const MlpArgs g)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *sm = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);
+    const int n = a.n, s = a.s, S = a.S, ns = a.ns;
+    const TcVecLayout lay = tc_vec_layout(L, KB0, n, ns);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t sbase = saddr(sm);
+    float *bias = reinterpret_cast<float *>(sm + lay.bias);
+    float *bout = reinterpret_cast<float *>(sm + lay.bout);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + lay.bars);
+    uint64_t *opu = bars + 0, *opx = bars + 2, *dnb = bars + 4, *payb = bars + 8, *finb = bars + 10;
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + lay.misc);
+    volatile int *abort = reinterpret_cast<volatile int *>(sm + lay.misc + 4);
+    double *red = reinterpret_cast<double *>(sm + lay.red);
+    double *bsum = reinterpret_cast<double *>(sm + lay.bsum);
+    const int in_pad = g.in_pad;
+
+    // weights into the swizzled operand layout (W_out: rows 0 .. kOut - 1)
+    for (int l = 0; l <= L; ++l) {
+        const int din = l == 0 ? in_pad : kH;
+        const int rows = l == L ? kOut : kH;
+        const int chunks = l == 0 ? KB0 * 8 : 16;
+        const __nv_bfloat16 *W = g.wh + (l == L ? g.off_wout : g.offW[l]);
+        const uint32_t base = l == 0 ? lay.w0 : (l == L ? lay.wo : lay.w + (l - 1) * 2 * kTileBytes);
+        for (int e = tid; e < rows * chunks; e += kThreads) {
+            const int h = e / chunks, c = e % chunks;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (c * 8 < din) v = *reinterpret_cast<const uint4 *>(W + (size_t)h * din + c * 8);
+            *reinterpret_cast<uint4 *>(sm + base + (c >> 3) * rows * 128 + (h >> 3) * 1024 + (h & 7) * 128 +
+                                       (((c & 7) ^ (h & 7)) << 4)) = v;
+        }
+    }
+    for (int e = tid; e < L * kH; e += kThreads) bias[e] = 0.5f * g.wp[g.offb[e / kH] + e % kH];
+    for (int e = tid; e < kOut; e += kThreads) bout[e] = g.wp[g.off_bout + e];
+    for (int e = tid; e < kGroups * 4 * n * ns; e += kThreads) bsum[e] = 0.0;
+    if (tid == 0) {
+        for (int gi = 0; gi < kGroups; ++gi) {
+            mbar_init(&opu[gi], 8);
+            mbar_init(&opx[gi], 8);
+            mbar_init(&dnb[gi], 1);
+            mbar_init(&payb[gi], 4);
+        }
+        mbar_init(finb, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    fence_async_smem();
+    if (warp == kEpiWarps) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
+                     "r"(kGroups * 2 * kH));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = *tslot;
+    const uint64_t ntiles = (a.paths + kGroups * kRows - 1) / (kGroups * kRows);
+
+    if (warp == kEpiWarps) {
+        // MMA issuer: per step and tile, L hidden products and the output product
+        // (job j into TMEM buffer j & 1 of the tile), tiles in turn
+        if (lane == 0) {
+            uint32_t phu[kGroups] = {0, 0}, phx[kGroups] = {0, 0};
+            uint64_t job = 0;
+            bool ok = !g.stall_mma;
+            for (uint64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+                for (int k = 0; ok && k < S; ++k) {
+                    for (int l = 0; ok && l <= L; ++l, ++job) {
+                        for (int gi = 0; gi < kGroups; ++gi) {
+                            uint64_t *ob = l == 0 ? &opu[gi] : &opx[gi];
+                            uint32_t &ph = l == 0 ? phu[gi] : phx[gi];
+                            if (!mbar_wait(ob, ph, abort, g.err)) { ok = false; break; }
+                            ph ^= 1;
+                            tc_after();
+                            const uint32_t d = tmem + gi * 2 * kH + (uint32_t)(job & 1) * kH;
+                            const uint32_t abase = sbase + (l == 0 ? lay.u + gi * KB0 * kTileBytes
+                                                                   : lay.x + gi * 2 * kTileBytes);
+                            const uint32_t bbase =
+                                sbase + (l == 0 ? lay.w0 : (l == L ? lay.wo : lay.w + (l - 1) * 2 * kTileBytes));
+                            const uint32_t bstride = l == L ? (uint32_t)kOutBlock : (uint32_t)kTileBytes;
+                            const uint32_t id = l == L ? idesc_n(kOut) : kIdesc;
+                            const int ks_n = l == 0 ? in_pad / 16 : kH / 16;
+                            for (int ks = 0; ks < ks_n; ++ks) {
+                                const uint32_t ao = (ks >> 2) * kTileBytes + (ks & 3) * 32;
+                                const uint32_t bo = (ks >> 2) * bstride + (ks & 3) * 32;
+                                mma_bf16_id(d, sdesc(abase + ao), sdesc(bbase + bo), id, ks > 0);
+                            }
+                            mma_commit(&dnb[gi]);
+                        }
+                    }
+                }
+            }
+            mma_commit(finb);
+            volatile int dummy_abort = 0;
+            mbar_wait(finb, 0, &dummy_abort, g.err);
+        }
+        __syncwarp();
+    } else {
+        const int gi = warp >> 3, hf = (warp >> 2) & 1, q4 = warp & 3;
+        const int row = q4 * 32 + lane;
+        const int T = kGroups * kRows;
+        const int col = gi * kRows + row;
+        const bool owner = hf == 0;
+        double *tred = red + (size_t)gi * 2 * 4 * ns * 2;
+        double *tsum = bsum + (size_t)gi * 4 * n * ns;
+        unsigned char *xptr = sm + lay.x + gi * 2 * kTileBytes;
+        unsigned char *uptr = sm + lay.u + gi * KB0 * kTileBytes;
+        const uint32_t dcol = tmem + ((uint32_t)(q4 * 32) << 16) + gi * 2 * kH;
+        float *st = a.state + (size_t)blockIdx.x * n * T + col;
+        const float h = a.h;
+        uint32_t phd = 0, php = 0;
+        uint64_t job = 0;
+        int mcount = 0;
+        bool ok = true;
+        for (uint64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
+            const uint64_t lp = tile * (uint64_t)T + col;
+            const bool active = lp < a.paths;
+            const uint64_t p = a.first_path + lp;
+            uint64_t sidx = ~0ull;
+            if (owner && a.snap != nullptr && active && lp % a.snap_stride == 0 && lp / a.snap_stride < a.n_snap)
+                sidx = lp / a.snap_stride;
+            if (owner)
+                for (int l = 0; l < n; ++l) st[(size_t)l * T] = 0.0f;
+            for (int k = 0; ok && k < S; ++k) {
+                const int imin = k / s + 1;
+                const bool mat = (k + 1) % s == 0;
+                float dH = 0.0f;
+                if (owner) {
+                    dH = draw_increment(a, p, (uint32_t)k);
+                    // feature row: column 0 t, 1 u_0 = 0, 1 + m u_m
+                    const float xt = (float)k * h * g.sc.t_scale;
+                    for (int c8 = 0; c8 < KB0 * 8; ++c8) {
+                        float f[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int c = c8 * 8 + e, m = c - 1;
+                            f[e] = c == 0 ? xt : ((m >= 1 && m <= n) ? st[(size_t)(m - 1) * T] * g.sc.u_scale : 0.0f);
+                        }
+                        *reinterpret_cast<uint4 *>(uptr + chunk_off(row, c8 >> 3, c8 & 7)) =
+                            make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+                    }
+                }
+                fence_async_smem();
+                tc_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&opu[gi]);
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    if (!ok) continue;
+                    if (!warp_wait(&dnb[gi], phd, abort, g.err)) { ok = false; continue; }
+                    phd ^= 1;
+                    tc_after();
+                    const uint32_t dbuf = dcol + (uint32_t)(job & 1) * kH + hf * 64;
+                    ++job;
+                    const float *hbl = bias + l * kH + hf * 64;
+                    uint32_t ra[16], rb[16];
+                    tmem_ld16(dbuf, ra);
+                    tmem_wait16(ra);
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) {
+                        uint32_t(&cur)[16] = (cc & 1) ? rb : ra;
+                        uint32_t(&nxt)[16] = (cc & 1) ? ra : rb;
+                        if (cc < 3) tmem_ld16(dbuf + (cc + 1) * 16, nxt);
+#pragma unroll
+                        for (int qd = 0; qd < 2; ++qd) {
+                            float sv[8];
+                            silu8(cur + qd * 8, hbl + cc * 16 + qd * 8, sv);
+                            *reinterpret_cast<uint4 *>(xptr + chunk_off(row, hf, cc * 2 + qd)) =
+                                make_uint4(pack2(sv[0], sv[1]), pack2(sv[2], sv[3]), pack2(sv[4], sv[5]),
+                                           pack2(sv[6], sv[7]));
+                        }
+                        if (cc < 3) tmem_wait16(nxt);
+                    }
+                    fence_async_smem();
+                    tc_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&opx[gi]);
+                }
+                // output product: every rate's f, read by the row's owner
+                if (ok && !warp_wait(&dnb[gi], phd, abort, g.err)) ok = false;
+                if (!ok) break;
+                phd ^= 1;
+                tc_after();
+                const uint32_t obuf = dcol + (uint32_t)(job & 1) * kH;
+                ++job;
+                if (owner) {
+                    uint32_t r0[16], r1[16], r2[16];
+                    tmem_ld16(obuf, r0);
+                    tmem_ld16(obuf + 16, r1);
+                    tmem_ld16(obuf + 32, r2);
+                    tmem_wait16(r0);
+                    tmem_wait16(r1);
+                    tmem_wait16(r2);
+                    float fo[kOut];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        fo[c] = __uint_as_float(r0[c]) + bout[c];
+                        fo[16 + c] = __uint_as_float(r1[c]) + bout[16 + c];
+                        fo[32 + c] = __uint_as_float(r2[c]) + bout[32 + c];
+                    }
+                    tc_before();
+                    // Euler step of every live rate with A_i = C_i + s_y f_{i-1}
+#pragma unroll
+                    for (int i = kOut; i >= 1; --i) {
+                        if (i > n || i < imin) continue;
+                        const size_t rowk = (size_t)k * n + (i - 1);
+                        float *sp = st + (size_t)(i - 1) * T;
+                        const float A = g.Ctab[rowk] + g.sc.y_scale * fo[i - 1];
+                        const float z = sp[0] + fmaf(a.row[rowk].x, dH, -A * h);
+                        sp[0] = z;
+                        if (mat && sidx != ~0ull)
+                            a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = z + a.Z0[i - 1];
+                    }
+                } else {
+                    tc_before();
+                }
+                if (mat && owner) {
+                    const int m = imin, buf = mcount & 1;
+                    ++mcount;
+                    double Pp, Sp;
+                    float Lm;
+                    maturity_products(a, m, [&](int i) { return st[(size_t)(i - 1) * T] + a.Z0[i - 1]; }, Pp, Sp, Lm);
+                    for (int qs = 0; qs < ns; ++qs) {
+                        const float K = a.strikes[(size_t)(m - 1) * ns + qs];
+                        const double pay = active ? payoff(a, Pp, Sp, Lm, K) : 0.0;
+                        const double s1 = warp_sum(pay);
+                        const double s2 = warp_sum(pay * pay);
+                        if (lane == 0) {
+                            tred[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 0] = s1;
+                            tred[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 1] = s2;
+                        }
+                    }
+                    if (lane == 0) mbar_arrive(&payb[gi]);
+                    if (q4 == 0) {
+                        if (!warp_wait(&payb[gi], php, abort, g.err)) { ok = false; break; }
+                        if (lane == 0) {
+                            for (int qs = 0; qs < ns; ++qs) {
+                                double s1 = 0.0, s2 = 0.0;
+                                for (int wv = 0; wv < 4; ++wv) {
+                                    s1 += tred[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 0];
+                                    s2 += tred[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 1];
+                                }
+                                double *acc = tsum + 4 * ((size_t)(m - 1) * ns + qs);
+                                kahan_add(acc + 0, acc + 1, s1);
+                                kahan_add(acc + 2, acc + 3, s2);
+                            }
+                        }
+                    }
+                    php ^= 1;
+                }
+            }
+        }
+    }
+    tc_before();
+    __syncthreads();
+    if (warp == kEpiWarps) {
+        tc_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kGroups * 2 * kH));
+    }
+    double *out = a.partials + (size_t)blockIdx.x * n * ns * 2;
+    for (int e = tid; e < n * ns; e += kThreads) {
+        out[2 * e + 0] = bsum[4 * e + 0] + bsum[4 * ((size_t)n * ns + e) + 0];
+        out[2 * e + 1] = bsum[4 * e + 2] + bsum[4 * ((size_t)n * ns + e) + 2];
+    }
+}
+
 typedef void (*TcKernelFn)(const PathArgs, const MlpArgs);
 
 TcKernelFn pick_tc(int L, int KB0)
@@ -582,7 +900,47 @@ TcKernelFn pick_tc(int L, int KB0)
     return nullptr;
 }
 
+TcKernelFn pick_tc_vec(int L, int KB0)
+{
+    if (KB0 != 1) return nullptr;
+    switch (L) {
+    case 2: return mlp_tc_vec_kernel<2, 1>;
+    case 3: return mlp_tc_vec_kernel<3, 1>;
+    case 4: return mlp_tc_vec_kernel<4, 1>;
+    default: return nullptr;
+    }
+}
+
 }  // namespace
+
+size_t mlp_tc_vec_smem(int layers, int in_pad, int n, int ns)
+{
+    return tc_vec_layout(layers, (in_pad + 63) / 64, n, ns).total;
+}
+
+bool mlp_tc_vec_supported(int hidden, int layers, int in_pad, int outputs, int n)
+{
+    return hidden == kH && outputs == kOut && n <= kOut && in_pad % 16 == 0 &&
+           pick_tc_vec(layers, (in_pad + 63) / 64) != nullptr;
+}
+
+int mlp_tc_vec_occupancy(int layers, int in_pad, size_t smem, int *blocks_per_sm)
+{
+    TcKernelFn f = pick_tc_vec(layers, (in_pad + 63) / 64);
+    if (!f) return (int)cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, kThreads, smem);
+}
+
+int launch_mlp_tc_vec(int layers, int in_pad, int grid, size_t smem, cudaStream_t st, const PathArgs &a,
+                      const MlpArgs &g)
+{
+    TcKernelFn f = pick_tc_vec(layers, (in_pad + 63) / 64);
+    if (!f) return (int)cudaErrorInvalidValue;
+    f<<<grid, kThreads, smem, st>>>(a, g);
+    return (int)cudaGetLastError();
+}
 
 int mlp_tc_threads() { return kThreads; }
 int mlp_tc_paths_per_block() { return kGroups * kRows; }

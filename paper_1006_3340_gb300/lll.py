@@ -33,7 +33,8 @@ class LLLError(RuntimeError):
 class lll_mlp_cfg(ctypes.Structure):
     _fields_ = [("hidden", ctypes.c_int), ("layers", ctypes.c_int), ("train_paths", ctypes.c_uint64),
                 ("records_per_path", ctypes.c_int), ("epochs", ctypes.c_int), ("batch", ctypes.c_int),
-                ("lr", ctypes.c_double), ("lr_final", ctypes.c_double), ("seed", ctypes.c_uint64)]
+                ("lr", ctypes.c_double), ("lr_final", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("head", ctypes.c_int)]
 
 
 class lll_nig(ctypes.Structure):
@@ -81,6 +82,8 @@ def load():
         "lll_kernel_ms": (I, [V, _fp, _fp]),
         "lll_build_nig_quadrature": (I, [lll_nig, ctypes.c_double, I, _dp, _dp]),
         "lll_mlp_init": (I, [V, I, I, U64]),
+        "lll_mlp_init_head": (I, [V, I, I, I, U64]),
+        "lll_mlp_shape": (I, [V, ctypes.POINTER(I), ctypes.POINTER(I)]),
         "lll_mlp_train": (I, [V, ctypes.POINTER(lll_mlp_cfg), _dp]),
         "lll_mlp_layout": (I, [V, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(I), ctypes.POINTER(I),
                                ctypes.POINTER(ctypes.c_size_t)]),
@@ -205,14 +208,25 @@ def lll_kernel_ms(ctx):
     return a.value, b.value
 
 
-def lll_mlp_init(ctx, hidden, layers, seed=0):
-    _check(load().lll_mlp_init(ctx, int(hidden), int(layers), int(seed)), ctx)
+def lll_mlp_init(ctx, hidden, layers, seed=0, head=0):
+    _check(load().lll_mlp_init_head(ctx, int(hidden), int(layers), int(head), int(seed)), ctx)
+
+
+def lll_mlp_init_head(ctx, hidden, layers, head, seed=0):
+    _check(load().lll_mlp_init_head(ctx, int(hidden), int(layers), int(head), int(seed)), ctx)
+
+
+def lll_mlp_shape(ctx):
+    """(head, outputs) of the context's network."""
+    h, o = ctypes.c_int(), ctypes.c_int()
+    _check(load().lll_mlp_shape(ctx, ctypes.byref(h), ctypes.byref(o)), ctx)
+    return h.value, o.value
 
 
 def lll_mlp_train(ctx, hidden=128, layers=3, train_paths=1 << 16, records_per_path=8, epochs=4,
-                  batch=8192, lr=2e-3, lr_final=2e-4, seed=7):
+                  batch=8192, lr=2e-3, lr_final=2e-4, seed=7, head=0):
     cfg = lll_mlp_cfg(int(hidden), int(layers), int(train_paths), int(records_per_path), int(epochs),
-                      int(batch), float(lr), float(lr_final), int(seed))
+                      int(batch), float(lr), float(lr_final), int(seed), int(head))
     loss = ctypes.c_double()
     _check(load().lll_mlp_train(ctx, ctypes.byref(cfg), ctypes.byref(loss)), ctx)
     return loss.value
@@ -243,7 +257,8 @@ def lll_mlp_params(ctx, direction, params=None, count=None, scales=None):
 def lll_mlp_eval(ctx, x, y=None, n_params=None, want_grads=False):
     x = np.ascontiguousarray(x, dtype=np.float32)
     rows = x.shape[0]
-    out = np.zeros(rows, dtype=np.float32)
+    head, outputs = lll_mlp_shape(ctx)
+    out = np.zeros((rows, outputs) if head else rows, dtype=np.float32)
     yy = None if y is None else np.ascontiguousarray(y, dtype=np.float32)
     g = np.zeros(n_params, dtype=np.float32) if want_grads else None
     loss = ctypes.c_double()

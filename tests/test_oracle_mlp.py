@@ -48,3 +48,29 @@ def test_adam_reduces_loss():
         params = mlp.adam_step(params, g, state, 3e-3, t)
     l1, _ = mlp.loss_and_grads(params, x, y)
     assert l1 < 0.1 * l0
+
+
+def test_vector_head_gradients_match_finite_differences():
+    """The vector head's loss is the MSE over the first n of its output
+    columns (the rates); the rest is padding and must get zero gradient."""
+    rng = np.random.default_rng(2)
+    n, O = 5, 8
+    params = mlp.init_params([6, 12, 12, O], seed=4)
+    x = rng.normal(size=(30, 6))
+    y = rng.normal(size=(30, O))
+    _, grads = mlp.loss_and_grads_vec(params, x, y, n)
+    eps = 1e-6
+    for li, (W, b) in enumerate(params):
+        for arr, g in ((W, grads[li][0]), (b, grads[li][1])):
+            flat, gflat = arr.reshape(-1), g.reshape(-1)
+            for idx in rng.choice(flat.size, size=min(10, flat.size), replace=False):
+                old = flat[idx]
+                flat[idx] = old + eps
+                lp, _ = mlp.loss_and_grads_vec(params, x, y, n)
+                flat[idx] = old - eps
+                lm, _ = mlp.loss_and_grads_vec(params, x, y, n)
+                flat[idx] = old
+                fd = (lp - lm) / (2 * eps)
+                assert abs(fd - gflat[idx]) <= 1e-6 * max(1.0, abs(fd)), (li, idx, fd, gflat[idx])
+    Wout, bout = grads[-1]
+    assert np.all(Wout[n:] == 0) and np.all(bout[n:] == 0)

@@ -135,3 +135,56 @@ def test_last_rate_feature_follows_linear_recursion():
     for k in range(n):
         D = D - s_y * s_u * h * (D + U0[:, k])
         assert np.abs((got[:, k, n - 1] - logL0) - (U0[:, k + 1] + D)).max() <= 1e-13
+
+
+# ---- vector head: one row per path, x = (t s_t, u_0 .. u_n), output column i - 1 for rate i
+
+
+def _zero_net_vec(in_dim, outputs, hidden=4, layers=3):
+    params = [(np.zeros((hidden, in_dim)), np.zeros(hidden))]
+    params += [(np.zeros((hidden, hidden)), np.zeros(hidden)) for _ in range(layers - 1)]
+    params.append((np.zeros((outputs, hidden)), np.zeros(outputs)))
+    return params
+
+
+def _feature_net_vec(in_dim, j, outputs, layers=3):
+    """Every output equals x_j exactly."""
+    params = _feature_net(in_dim, j, layers)[:-1]
+    params.append((np.tile(np.array([[1.0, -1.0]]), (outputs, 1)), np.zeros(outputs)))
+    return params
+
+
+def test_vector_head_zero_network_one_rate_is_full_scheme():
+    wl = workloads.tiny(N=2, s=5, Q=8, paths=48)
+    m = _model(wl)
+    got = mlp.simulate_scheme(m, _zero_net_vec(1 + wl.N, 16), SCALES, npaths=wl.paths, head=1)
+    ref = ora.simulate(m, ora.FULL, npaths=wl.paths, want_snap=True)
+    assert np.nanmax(np.abs(got["snap"] - ref["snap"])) <= 1e-12
+
+
+def test_vector_head_time_feature_shifts_drift_by_closed_form():
+    wl = workloads.tiny(N=5, s=3, Q=8, paths=16)
+    m = _model(wl)
+    base = mlp.simulate_scheme(m, _zero_net_vec(1 + wl.N, 16), SCALES, npaths=wl.paths, head=1)["snap"]
+    got = mlp.simulate_scheme(m, _feature_net_vec(1 + wl.N, 0, 16), SCALES, npaths=wl.paths, head=1)["snap"]
+    s_t, s_y, h = SCALES[0], SCALES[4], wl.h
+    for mat in range(1, wl.n + 1):
+        shift = -s_y * s_t * h * np.sum(np.arange(mat * wl.s) * h)
+        assert np.abs(got[:, mat - 1, mat - 1:] - base[:, mat - 1, mat - 1:] - shift).max() <= 1e-13
+
+
+def test_vector_head_last_rate_feature_follows_linear_recursion():
+    wl = workloads.tiny(N=4, s=1, Q=8, paths=8)
+    m = _model(wl)
+    n = wl.n
+    in_dim = 1 + wl.N
+    col = 1 + n  # u_n
+    base = mlp.simulate_scheme(m, _zero_net_vec(in_dim, 16), SCALES, npaths=wl.paths, head=1)["snap"]
+    got = mlp.simulate_scheme(m, _feature_net_vec(in_dim, col, 16), SCALES, npaths=wl.paths, head=1)["snap"]
+    s_u, s_y, h = SCALES[3], SCALES[4], wl.h
+    logL0 = np.log(wl.L0[n])
+    U0 = np.concatenate([np.zeros((wl.paths, 1)), base[:, :, n - 1] - logL0], axis=1)
+    D = np.zeros(wl.paths)
+    for k in range(n):
+        D = D - s_y * s_u * h * (D + U0[:, k])
+        assert np.abs((got[:, k, n - 1] - logL0) - (U0[:, k + 1] + D)).max() <= 1e-13
