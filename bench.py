@@ -39,6 +39,11 @@ def _workload(args):
     return wl
 
 
+def _code(s):
+    """Library scheme of a bench scheme name ("mlp_vec": LLL_MLP with the vector-head network)."""
+    return "mlp" if s == "mlp_vec" else s
+
+
 def _describe(wl, schemes):
     return (f"{wl.name}: N={wl.N} (n={wl.n} rates) delta={wl.delta} s={wl.s} Q={wl.Q} "
             f"NIG({wl.alpha},{wl.beta},{wl.dbar}) {wl.paths} paths/GPU, "
@@ -232,6 +237,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     mlp_info = None
     mlp_params = None
+    mlp_vec_params = None
     if "mlp" in schemes:
         # The learned compensator is trained once, on its own paths (seed 7),
         # with the project's GPU kernels; the timed steps then price with it.
@@ -247,11 +253,25 @@ def main():
                     "arch": f"{in_dim}->128x3->1 SiLU, BF16 weights, FP32 accumulate",
                     "train_pairs": "2^16 paths x 8 recorded steps x live rates (~1e7)"}
 
+    if "mlp_vec" in schemes:
+        # the vector-head network: one pass per path and step gives every rate's compensator
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lossv = lll.lll_mlp_train(sims["mlp_vec"].ctx, hidden=128, layers=3, train_paths=1 << 16,
+                                  records_per_path=8, epochs=40, batch=4096, lr=2e-3, lr_final=1e-4, seed=7,
+                                  head=1)
+        torch.cuda.synchronize()
+        nv, in_dim_v, _, _ = lll.lll_mlp_layout(sims["mlp_vec"].ctx, 3)
+        mlp_vec_params = lll.lll_mlp_params(sims["mlp_vec"].ctx, 0, count=nv)
+        mlp_info = dict(mlp_info or {}, vec={"train_s": time.perf_counter() - t0, "final_loss_scaled": lossv,
+                                              "params": int(nv),
+                                              "arch": f"{in_dim_v}->128x3->48 SiLU (vector head), BF16, FP32 acc"})
+
     def one_step(evs=None):
         for i, s in enumerate(schemes):
             if evs is not None:
                 evs[i][0].record()
-            lll.lll_simulate(sims[s].ctx, lll.SCHEMES[s], first, wl.paths, wl.seed)
+            lll.lll_simulate(sims[s].ctx, lll.SCHEMES[_code(s)], first, wl.paths, wl.seed)
             if evs is not None:
                 evs[i][1].record()
 
@@ -328,6 +348,10 @@ def main():
         m1, m2, mcnt = shard.merge_sums(s1, s2, cnt)
         per["picard_merged_paths"] = mcnt
         per["picard_merged_atm_T10y"] = float(m1[n - 1, ns // 2] / mcnt)
+    if "mlp_vec" in per and "full" in per:
+        pv, _ = sims["mlp_vec"].prices()
+        pf, _ = sims["full"].prices()
+        per["mlp_vec_vs_full_max_bp"] = float(np.abs(pv - pf).max() * 1e4)
     if "mlp" in per and "full" in per:
         pm, _ = sims["mlp"].prices()
         pf, _ = sims["full"].prices()
@@ -356,21 +380,39 @@ def main():
             r["frac_at_sampled_clock"] = ach / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
         return r
 
-    def mlp_roofline():
-        ms = statistics.mean(per_scheme_ms["mlp"])
-        in_pad = 48 if wl.N + 3 <= 48 else 64
-        macs = in_pad * 128 + 128 * 128 * 2 + 128
-        ach = units * 2 * macs / (ms * 1e-3) / 1e12
-        peak = float(peaks.get("bf16_tflops_sustained", 1679.9))
-        return {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": (_traffic("mlp/L3/KT3" if args.mlp_kernel == "warp" else "mlp_tc/L3/KB1")
-                            if wl.paths == 1 << 20 else None),
-                "kernel": ("mlp path kernel (mma.sync bf16)" if args.mlp_kernel == "warp" or wl.N + 3 > 64
-                           else "mlp path kernel (tcgen05 bf16, TMEM accumulators)"),
-                "peak_basis": "bf16_tflops_sustained of MEASURED_PEAKS"}
+    # MUFU (special function unit) rate of tanh.approx.f32, measured on this GPU by a
+    # probe: 16 per SM per clock (ex2 runs at 32); every SiLU of the network costs one.
+    sfu_peak = sms * 16 * sm_max * 1e6 / 1e12  # T tanh/s at the maximum SM clock
+
+    def mlp_roofline(s="mlp"):
+        """The learned drift: the binding pipe is MUFU (one tanh per SiLU), the
+        tensor pipe is reported beside it."""
+        ms = statistics.mean(per_scheme_ms[s])
+        t = ms * 1e-3
+        if s == "mlp":
+            in_pad = 48 if wl.N + 3 <= 48 else 64
+            flop = units * 2 * (in_pad * 128 + 128 * 128 * 2 + 128)  # per (path, rate, step) row
+            silu = units * 3 * 128
+        else:
+            path_steps = wl.paths * wl.steps * world
+            flop = path_steps * 2 * (48 * 128 + 128 * 128 * 2 + 128 * 48)  # one pass per (path, step)
+            silu = path_steps * 3 * 128
+        tflops = flop / t / 1e12
+        bf16 = float(peaks.get("bf16_tflops_sustained", 1679.9))
+        ach = silu / t / 1e12
+        key = "mlp/L3/KT3" if args.mlp_kernel == "warp" else "mlp_tc/L3/KB1"
+        return {"bound": "alu", "pipe": "MUFU tanh.approx (SiLU)", "achieved": ach, "peak": sfu_peak,
+                "unit": "T tanh/s", "frac": ach / sfu_peak,
+                "peak_basis": f"{sms} SMs x 16 tanh/clk (probe on this GPU) x {sm_max:.0f} MHz",
+                "tensor_tflops": tflops, "tensor_frac": tflops / bf16,
+                "tensor_peak_basis": "bf16_tflops_sustained of MEASURED_PEAKS",
+                "traffic": _traffic(key) if (s == "mlp" and wl.paths == 1 << 20) else None,
+                "kernel": ("mlp path kernel (mma.sync bf16)" if s == "mlp" and (args.mlp_kernel == "warp" or wl.N + 3 > 64)
+                           else "mlp path kernel (tcgen05 bf16, TMEM accumulators)"
+                           + (", vector head" if s == "mlp_vec" else ""))}
 
     dom = max(schemes, key=lambda s: statistics.mean(per_scheme_ms[s]))
-    roofline = mlp_roofline() if dom == "mlp" else quad_roofline(dom)
+    roofline = mlp_roofline(dom) if dom in ("mlp", "mlp_vec") else (quad_roofline(dom) if dom in ("picard", "full") else None)
 
     # end to end through the C ABI from host arrays: init (H2D of the model
     # inputs, FP64 tables on the GPU), strikes, each scheme, prices (D2H).
@@ -379,6 +421,8 @@ def main():
         h2d = (wl.L0.nbytes + wl.lam.nbytes + x.nbytes + W.nbytes) * len(schemes) + wl.strikes.nbytes * len(schemes)
         if mlp_params is not None:
             h2d += mlp_params[0].nbytes + mlp_params[1].nbytes
+        if mlp_vec_params is not None:
+            h2d += mlp_vec_params[0].nbytes + mlp_vec_params[1].nbytes
         d2h = len(schemes) * 2 * n * ns * 8
         ts = []
         for k in range(max(2, args.steps)):
@@ -392,7 +436,10 @@ def main():
                     lll.lll_mlp_init(sim.ctx, 128, 3, 0)
                     lll.lll_mlp_params(sim.ctx, 1, mlp_params[0], scales=mlp_params[1])
                     lll.lll_mlp_set_kernel(sim.ctx, args.mlp_kernel)
-                lll.lll_simulate(sim.ctx, lll.SCHEMES[s], first, wl.paths, wl.seed)
+                if s == "mlp_vec":
+                    lll.lll_mlp_init(sim.ctx, 128, 3, 0, head=1)
+                    lll.lll_mlp_params(sim.ctx, 1, mlp_vec_params[0], scales=mlp_vec_params[1])
+                lll.lll_simulate(sim.ctx, lll.SCHEMES[_code(s)], first, wl.paths, wl.seed)
                 sim.prices()
                 sim.close()
             torch.cuda.synchronize()
@@ -420,6 +467,7 @@ def main():
                            f"({L2_FLUSH_BYTES >> 20} MiB write outside the events)"},
                 "per_scheme": per, "roofline": roofline,
                 "roofline_picard": quad_roofline("picard") if "picard" in schemes else None,
+                "roofline_mlp_vec": mlp_roofline("mlp_vec") if "mlp_vec" in schemes else None,
                 "mlp": mlp_info, "autotuned": tuned, "cpu_baseline": cpu, "e2e": e2e,
                 "clocks": clocks, "gpu_launches": 2 * len(schemes) * args.steps}
         print(json.dumps(line), flush=True)
