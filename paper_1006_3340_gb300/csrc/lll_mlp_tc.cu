@@ -43,7 +43,7 @@ namespace {
 constexpr int kH = 128;               // hidden width
 constexpr int kRows = 128;            // rows (paths) per warpgroup tile
 constexpr int kGroups = 2;            // path tiles in flight per CTA
-constexpr int kEpiWarps = 8 * kGroups; // per tile: 4 lane quadrants x 2 column halves
+constexpr int kEpiWarps = 8 * kGroups; // 4 TMEM lane quadrants x 4 column quarters (vector head: x 2 halves x 2 tiles)
 constexpr int kThreads = (kEpiWarps + 1) * 32;
 constexpr int kTileBytes = kRows * 128; // one 64-wide K block of a 128-row operand
 constexpr long long kWaitBudget = 4000000000ll; // clock cycles (about 2 s)
@@ -72,6 +72,8 @@ __device__ __forceinline__ uint32_t chunk_off(int r, int kb, int c8)
 {
     return (uint32_t)(kb * kTileBytes + (r >> 3) * 1024 + (r & 7) * 128 + ((c8 ^ (r & 7)) << 4));
 }
+
+__device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi)
 {
@@ -164,6 +166,24 @@ __device__ __forceinline__ void mma_bf16_id(uint32_t d, uint64_t ad, uint64_t bd
                  "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
 
+// A operand in tensor memory: 128 lanes (rows) x 8 columns, each column two
+// BF16 values of consecutive K (lower K in the low half).
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d, uint32_t at, uint64_t bd, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+                 "r"(at), "l"(bd), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t ta, const uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 __device__ __forceinline__ void mma_commit(uint64_t *b)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(b))
@@ -224,7 +244,7 @@ __device__ __forceinline__ void kahan_add(double *s, double *c, double x)
 
 // Shared-memory plan; operand tiles first (1024-byte aligned).
 struct TcLayout {
-    uint32_t w0, w, u, x, bias, wout, bars, misc, opart, red, bsum, total;
+    uint32_t w0, w, u, bias, w0c, hbw, wout, bars, misc, opart, red, bsum, total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int L, int KB0, int n, int ns)
@@ -233,13 +253,14 @@ __host__ __device__ inline TcLayout tc_layout(int L, int KB0, int n, int ns)
     uint32_t o = 0;
     t.w0 = o; o += KB0 * kTileBytes;             // W_0: H rows x 64 KB0 columns
     t.w = o; o += (L - 1) * 2 * kTileBytes;       // W_1 .. W_{L-1}: H rows x 128 columns
-    t.u = o; o += kGroups * KB0 * kTileBytes;     // feature rows, per tile
-    t.x = o; o += kGroups * 2 * kTileBytes;       // hidden activations, per tile
+    t.u = o; o += kGroups * KB0 * kTileBytes;     // feature rows, per tile (hidden activations live in TMEM)
     t.bias = o; o += L * kH * 4;                  // b_0 / 2 .. b_{L-1} / 2
+    t.w0c = o; o += 3 * kH * 4;                   // W_0 columns of t, i, lambda, halved
+    t.hbw = o; o += kEpiWarps * 64 * 4;           // per warp: first-layer half bias of the current rate
     t.wout = o; o += kH * 4;                      // output weights (BF16 values)
     t.bars = o; o += 12 * 8;                      // mbarriers
     t.misc = o; o += 16;                          // TMEM base, abort word
-    t.opart = o; o += kGroups * kRows * 4;        // output partial of the upper column half
+    t.opart = o; o += kGroups * 3 * kRows * 4;    // output partials of column quarters 1..3, per tile
     o = (o + 15) & ~15u;
     t.red = o; o += kGroups * 2 * 4 * ns * 2 * 8; // per tile: 4 owner warps' payoff sums, two buffers
     t.bsum = o; o += kGroups * n * ns * 4 * 8;    // per tile: Kahan accumulators
@@ -258,6 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
     const uint32_t sbase = saddr(sm);
     float *bias = reinterpret_cast<float *>(sm + lay.bias);
     float *wout = reinterpret_cast<float *>(sm + lay.wout);
+    float *w0c = reinterpret_cast<float *>(sm + lay.w0c);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + lay.bars);
     // Operand-ready barriers, one arrival per warp of the tile: feature rows
     // (first layer) and activations (hidden layers) have separate barriers, so
@@ -286,19 +308,27 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
             const int h = e / chunks, c = e % chunks;
             uint4 v = make_uint4(0, 0, 0, 0);
             if (c * 8 < din) v = *reinterpret_cast<const uint4 *>(W + (size_t)h * din + c * 8);
+            if (l == 0 && c == 0) {
+                // columns t, i, lambda_i: the same for every path of a (step, rate),
+                // so they enter through the per-rate bias instead of the product
+                v.x = 0u;
+                v.y &= 0xffff0000u;
+            }
             *reinterpret_cast<uint4 *>(sm + base + chunk_off(h, c >> 3, c & 7)) = v;
         }
     }
     for (int e = tid; e < L * kH; e += kThreads) bias[e] = 0.5f * g.wp[g.offb[e / kH] + e % kH]; // half biases
     for (int e = tid; e < kH; e += kThreads) wout[e] = __bfloat162float(g.wh[g.off_wout + e]);
+    for (int e = tid; e < 3 * kH; e += kThreads)
+        w0c[e] = 0.5f * __bfloat162float(g.wh[g.offW[0] + (size_t)(e % kH) * g.in_pad + e / kH]);
     for (int e = tid; e < kGroups * 4 * n * ns; e += kThreads) bsum[e] = 0.0;
     if (tid == 0) {
         for (int gi = 0; gi < kGroups; ++gi) {
-            mbar_init(&opu[gi], 8);   // the 8 warps of the tile
-            mbar_init(&opx[gi], 8);
+            mbar_init(&opu[gi], kEpiWarps); // every epilogue warp
+            mbar_init(&opx[gi], kEpiWarps);
             mbar_init(&dnb[gi], 1);
-            mbar_init(&outb[gi], 4);  // the 4 upper-half warps
-            mbar_init(&payb[gi], 4);  // the 4 path-owning warps
+            mbar_init(&outb[gi], 12);       // the warps of column quarters 1..3
+            mbar_init(&payb[gi], 4);        // the 4 path-owning warps (payb[0] only)
         }
         mbar_init(finb, 1);
         *abort = 0;
@@ -318,40 +348,46 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
 
     if (warp == kEpiWarps) {
         // ---------------- MMA issuer ----------------
-        // Job j of a tile (its L products per live rate and step, in layer
-        // order) accumulates into TMEM buffer j & 1 of the tile, so the next
-        // rate's first-layer product can run while the epilogue still reads
-        // the current rate's last layer.  The tiles are served in turn.
+        // Per live rate and tile: the first layer (feature rows in shared
+        // memory; the rate's own inputs t, i, lambda_i enter through a per-rate
+        // bias, so the rows change once per step), then the hidden layers with
+        // the activations as the A operand in tensor memory.  Each tile's
+        // accumulator is TMEM columns [128 gi, 128 gi + 128), its activations
+        // [256 + 64 gi, 256 + 64 gi + 64).  The tiles are served in turn.
         if (lane == 0) {
             uint32_t phu[kGroups] = {0, 0}, phx[kGroups] = {0, 0};
-            uint64_t job = 0;
             bool ok = !g.stall_mma; // stalled: nothing is issued, the epilogue's waits run out
-            for (uint64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-                for (int k = 0; ok && k < S; ++k) {
-                    const int live = n - (k / s + 1) + 1;
-                    for (int r = 0; ok && r < live; ++r) {
-                        for (int l = 0; ok && l < L; ++l, ++job) {
-                            for (int gi = 0; gi < kGroups; ++gi) {
-                                uint64_t *ob = l == 0 ? &opu[gi] : &opx[gi];
-                                uint32_t &ph = l == 0 ? phu[gi] : phx[gi];
-                                if (!mbar_wait(ob, ph, abort, g.err)) { ok = false; break; }
-                                ph ^= 1;
-                                tc_after();
-                                const uint32_t d = tmem + gi * 2 * kH + (uint32_t)(job & 1) * kH;
-                                const uint32_t abase = sbase + (l == 0 ? lay.u + gi * KB0 * kTileBytes
-                                                                       : lay.x + gi * 2 * kTileBytes);
-                                const uint32_t bbase = sbase + (l == 0 ? lay.w0 : lay.w + (l - 1) * 2 * kTileBytes);
-                                const int ks_n = l == 0 ? in_pad / 16 : kH / 16;
-                                for (int ks = 0; ks < ks_n; ++ks) {
-                                    const uint32_t off = (ks >> 2) * kTileBytes + (ks & 3) * 32;
-                                    mma_bf16(d, sdesc(abase + off), sdesc(bbase + off), ks > 0);
-                                }
-                                mma_commit(&dnb[gi]);
-                            }
-                        }
+            auto issue = [&](int gi, int l) {
+                uint64_t *ob = l == 0 ? &opu[gi] : &opx[gi];
+                uint32_t &ph = l == 0 ? phu[gi] : phx[gi];
+                if (!mbar_wait(ob, ph, abort, g.err)) return false;
+                ph ^= 1;
+                tc_after();
+                const uint32_t d = tmem + gi * kH;
+                const uint32_t bbase = sbase + (l == 0 ? lay.w0 : lay.w + (l - 1) * 2 * kTileBytes);
+                if (l == 0) {
+                    const uint32_t abase = sbase + lay.u + gi * KB0 * kTileBytes;
+                    for (int ks = 0; ks < in_pad / 16; ++ks) {
+                        const uint32_t off = (ks >> 2) * kTileBytes + (ks & 3) * 32;
+                        mma_bf16(d, sdesc(abase + off), sdesc(bbase + off), ks > 0);
+                    }
+                } else {
+                    const uint32_t at = tmem + 2 * kH + gi * (kH / 2);
+                    for (int ks = 0; ks < kH / 16; ++ks) {
+                        const uint32_t off = (ks >> 2) * kTileBytes + (ks & 3) * 32;
+                        mma_bf16_ts(d, at + ks * 8, sdesc(bbase + off), ks > 0);
                     }
                 }
-            }
+                mma_commit(&dnb[gi]);
+                return true;
+            };
+            for (uint64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x)
+                for (int k = 0; ok && k < S; ++k) {
+                    const int live = n - (k / s + 1) + 1;
+                    for (int r = 0; ok && r < live; ++r)
+                        for (int l = 0; ok && l < L; ++l)
+                            for (int gi = 0; ok && gi < kGroups; ++gi) ok = issue(gi, l);
+                }
             // drain: the commit below completes only after every MMA issued above
             mma_commit(finb);
             volatile int dummy_abort = 0;
@@ -360,197 +396,216 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
         __syncwarp();
     } else {
         // ---------------- epilogue warps ----------------
-        // warp = 8 gi + 4 hf + q4: tile gi, column half hf (columns 64 hf .. 64 hf + 63),
-        // TMEM lane quadrant q4.  The hf = 0 thread of a row owns the path.
-        const int gi = warp >> 3, hf = (warp >> 2) & 1, q4 = warp & 3;
+        // warp = 4 cq + q4: TMEM lane quadrant q4 (row 32 q4 + lane of each tile)
+        // and column quarter cq (columns 32 cq .. 32 cq + 31).  Every warp works
+        // on both tiles, one layer at a time in tile order, so that one tile's
+        // product runs on the tensor pipe while the other tile's epilogue runs.
+        // The cq = 0 thread of a row owns that row's path in both tiles.
+        const int cq = warp >> 2, q4 = warp & 3;
         const int row = q4 * 32 + lane;          // TMEM lane = tile row
-        const int T = kGroups * kRows;           // paths per CTA tile
-        const int col = gi * kRows + row;        // column of this path in the state slot
-        const bool owner = hf == 0;
-        double *tred = red + (size_t)gi * 2 * 4 * ns * 2;   // this tile's warp sums
-        double *tsum = bsum + (size_t)gi * 4 * n * ns;       // this tile's accumulators
-        unsigned char *xptr = sm + lay.x + gi * 2 * kTileBytes;
-        const uint32_t dcol = tmem + ((uint32_t)(q4 * 32) << 16) + gi * 2 * kH + hf * 64; // + buffer * kH
-        float *st = a.state + (size_t)blockIdx.x * n * T + col;
+        const int T = kGroups * kRows;           // paths per CTA tile pair
+        const bool owner = cq == 0;
+        const uint32_t dq = tmem + ((uint32_t)(q4 * 32) << 16) + cq * 32;          // + tile * kH: accumulator
+        const uint32_t aq = tmem + ((uint32_t)(q4 * 32) << 16) + 2 * kH + cq * 16; // + tile * kH / 2: activations
+        float *hbw = reinterpret_cast<float *>(sm + lay.hbw) + warp * 32;
+        float *st = a.state + (size_t)blockIdx.x * n * T + row; // + tile * kRows
         const float h = a.h;
         const float b_out = g.wp[g.off_bout];
-        uint32_t phd = 0, pho = 0, php = 0;
-        uint64_t job = 0; // this tile's product count: TMEM buffer = job & 1
+        uint32_t phd[kGroups] = {0, 0}, pho[kGroups] = {0, 0}, php = 0;
         int mcount = 0;
         bool ok = true;
         for (uint64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-            const uint64_t lp = tile * (uint64_t)T + col;
-            const bool active = lp < a.paths;
-            const uint64_t p = a.first_path + lp;
-            uint64_t sidx = ~0ull;
-            if (owner && a.snap != nullptr && active && lp % a.snap_stride == 0 && lp / a.snap_stride < a.n_snap)
-                sidx = lp / a.snap_stride;
-            if (owner)
-                for (int l = 0; l < n; ++l) st[(size_t)l * T] = 0.0f;
+            uint64_t p[kGroups], sidx[kGroups];
+            bool active[kGroups];
+#pragma unroll
+            for (int gi = 0; gi < kGroups; ++gi) {
+                const uint64_t lp = tile * (uint64_t)T + gi * kRows + row;
+                active[gi] = lp < a.paths;
+                p[gi] = a.first_path + lp;
+                sidx[gi] = ~0ull;
+                if (owner && a.snap != nullptr && active[gi] && lp % a.snap_stride == 0 &&
+                    lp / a.snap_stride < a.n_snap)
+                    sidx[gi] = lp / a.snap_stride;
+                if (owner)
+                    for (int l = 0; l < n; ++l) st[(size_t)l * T + gi * kRows] = 0.0f;
+            }
 
             for (int k = 0; ok && k < S; ++k) {
                 const int imin = k / s + 1;
                 const bool mat = (k + 1) % s == 0;
-                float dH = 0.0f;
-                uint32_t u14[2] = {0, 0}; // BF16 u_1 .. u_4 (columns 4 .. 7)
+                float dH[kGroups] = {0.0f, 0.0f};
                 const float xt = (float)k * h * g.sc.t_scale;
                 if (owner) {
-                    dH = draw_increment(a, p, (uint32_t)k);
-                    // feature row of this path at t_k: u_m at column 3 + m (u_0 = 0)
-                    for (int c8 = 1; c8 < KB0 * 8; ++c8) {
-                        float f[8];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const int m = c8 * 8 + e - 3;
-                            f[e] = (m >= 1 && m <= n) ? st[(size_t)(m - 1) * T] * g.sc.u_scale : 0.0f;
+                    for (int gi = 0; gi < kGroups; ++gi) {
+                        const float *sg = st + gi * kRows;
+                        unsigned char *ug = sm + lay.u + gi * KB0 * kTileBytes;
+                        dH[gi] = draw_increment(a, p[gi], (uint32_t)k);
+                        // feature row of this path at t_k: u_m at column 3 + m (u_0 = 0); the
+                        // columns of t, i, lambda_i stay zero (they enter through the per-rate bias)
+                        for (int c8 = 0; c8 < KB0 * 8; ++c8) {
+                            float f[8];
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                const int m = c8 * 8 + e - 3;
+                                f[e] = (m >= 1 && m <= n) ? sg[(size_t)(m - 1) * T] * g.sc.u_scale : 0.0f;
+                            }
+                            *reinterpret_cast<uint4 *>(ug + chunk_off(row, c8 >> 3, c8 & 7)) =
+                                make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
                         }
-                        *reinterpret_cast<uint4 *>(sm + lay.u + gi * KB0 * kTileBytes + chunk_off(row, c8 >> 3, c8 & 7)) =
-                            make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
                     }
-                    float f[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) f[e] = (e + 1 <= n) ? st[(size_t)e * T] * g.sc.u_scale : 0.0f;
-                    u14[0] = pack2(f[0], f[1]);
-                    u14[1] = pack2(f[2], f[3]);
                 }
-                float lam_c = 0.0f, C_c = 0.0f;
-                if (owner) {
-                    lam_c = a.row[(size_t)k * n + (n - 1)].x;
-                    C_c = g.Ctab[(size_t)k * n + (n - 1)];
-                }
-                // columns 0..7 of rate i's feature row: t, i, lambda_i, u_0 = 0, u_1 .. u_4
-                unsigned char *urow0 = sm + lay.u + gi * KB0 * kTileBytes + chunk_off(row, 0, 0);
-                if (owner)
-                    *reinterpret_cast<uint4 *>(urow0) =
-                        make_uint4(pack2(xt, (float)n * g.sc.i_scale), pack2(lam_c * g.sc.lam_scale, 0.0f), u14[0],
-                                   u14[1]);
+                float lam_c = a.row[(size_t)k * n + (n - 1)].x, C_c = 0.0f; // every warp: lambda_i enters the bias
+                if (owner) C_c = g.Ctab[(size_t)k * n + (n - 1)];
+                // feature rows written and (after the previous step's last rate) the
+                // accumulators free: the first rate's first-layer products may start
                 fence_async_smem();
                 tc_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&opu[gi]);
+                if (lane == 0)
+                    for (int gi = 0; gi < kGroups; ++gi) mbar_arrive(&opu[gi]);
+                const float xt_b = bf16_round(xt);
                 for (int i = n; ok && i >= imin; --i) {
                     const size_t rowk = (size_t)k * n + (i - 1);
-                    float *sp = st + (size_t)(i - 1) * T;
-                    float zold = 0.0f, lam_n = 0.0f, C_n = 0.0f;
+                    float zold[kGroups] = {0.0f, 0.0f};
+                    float lam_n = 0.0f, C_n = 0.0f;
+                    if (i > imin) lam_n = a.row[rowk - 1].x;
                     if (owner) {
-                        zold = sp[0];
-                        if (i > imin) {
-                            lam_n = a.row[rowk - 1].x;
-                            C_n = g.Ctab[rowk - 1];
-                        }
+#pragma unroll
+                        for (int gi = 0; gi < kGroups; ++gi) zold[gi] = st[(size_t)(i - 1) * T + gi * kRows];
+                        if (i > imin) C_n = g.Ctab[rowk - 1];
                     }
-                    float o4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                    {
+                        // half first-layer bias of rate i for this warp's 32 columns:
+                        // (b_0 + W_0[:, t] t + W_0[:, i] i + W_0[:, lambda] lambda_i) / 2,
+                        // the inputs rounded to BF16 as the feature row would hold them
+                        const float xi_b = bf16_round((float)i * g.sc.i_scale);
+                        const float xl_b = bf16_round(lam_c * g.sc.lam_scale);
+                        const int c = cq * 32 + lane;
+                        hbw[lane] = fmaf(w0c[2 * kH + c], xl_b, fmaf(w0c[kH + c], xi_b, fmaf(w0c[c], xt_b, bias[c])));
+                        __syncwarp();
+                    }
+                    float opart_own[kGroups] = {0.0f, 0.0f};
 #pragma unroll
                     for (int l = 0; l < L; ++l) {
-                        if (!ok) continue;
-                        if (!warp_wait(&dnb[gi], phd, abort, g.err)) { ok = false; continue; }
-                        phd ^= 1;
-                        tc_after();
-                        const uint32_t dbuf = dcol + (uint32_t)(job & 1) * kH;
-                        ++job;
-                        const float *hbl = bias + l * kH + hf * 64;
-                        uint32_t ra[16], rb[16];
-                        tmem_ld16(dbuf, ra);
-                        tmem_wait16(ra);
 #pragma unroll
-                        for (int cc = 0; cc < 4; ++cc) {
-                            // columns 64 hf + 16 cc .. +15; the next chunk loads meanwhile
-                            uint32_t(&cur)[16] = (cc & 1) ? rb : ra;
-                            uint32_t(&nxt)[16] = (cc & 1) ? ra : rb;
-                            if (cc < 3) tmem_ld16(dbuf + (cc + 1) * 16, nxt);
+                        for (int gi = 0; gi < kGroups; ++gi) {
+                            if (!ok) continue;
+                            if (!warp_wait(&dnb[gi], phd[gi], abort, g.err)) { ok = false; continue; }
+                            phd[gi] ^= 1;
+                            tc_after();
+                            const uint32_t dbuf = dq + gi * kH;
+                            const float *hbl = l == 0 ? hbw : bias + l * kH + cq * 32;
+                            float o4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+                            uint32_t ra[16], rb[16];
+                            tmem_ld16(dbuf, ra);
+                            tmem_wait16(ra);
+                            tmem_ld16(dbuf + 16, rb);
 #pragma unroll
-                            for (int qd = 0; qd < 2; ++qd) {
-                                float sv[8];
-                                silu8(cur + qd * 8, hbl + cc * 16 + qd * 8, sv);
-                                if (l < L - 1) {
-                                    // K block hf, 16-byte chunk 2 cc + qd
-                                    *reinterpret_cast<uint4 *>(xptr + chunk_off(row, hf, cc * 2 + qd)) =
-                                        make_uint4(pack2(sv[0], sv[1]), pack2(sv[2], sv[3]), pack2(sv[4], sv[5]),
-                                                   pack2(sv[6], sv[7]));
-                                } else {
-                                    const float *wo = wout + hf * 64 + cc * 16 + qd * 8;
+                            for (int cc = 0; cc < 2; ++cc) {
+                                // columns 32 cq + 16 cc .. +15; the second chunk loads meanwhile
+                                uint32_t(&cur)[16] = cc ? rb : ra;
+                                uint32_t pk[8];
 #pragma unroll
-                                    for (int e = 0; e < 8; e += 2) {
-                                        // BF16 activations (packed round to nearest even), FP32 products
-                                        const uint32_t pk = pack2(sv[e], sv[e + 1]);
-                                        o4[e & 3] = fmaf(__uint_as_float(pk << 16), wo[e], o4[e & 3]);
-                                        o4[(e + 1) & 3] = fmaf(__uint_as_float(pk & 0xffff0000u), wo[e + 1], o4[(e + 1) & 3]);
+                                for (int qd = 0; qd < 2; ++qd) {
+                                    float sv[8];
+                                    silu8(cur + qd * 8, hbl + cc * 16 + qd * 8, sv);
+                                    if (l < L - 1) {
+#pragma unroll
+                                        for (int e = 0; e < 4; ++e) pk[qd * 4 + e] = pack2(sv[2 * e], sv[2 * e + 1]);
+                                    } else {
+                                        const float *wo = wout + cq * 32 + cc * 16 + qd * 8;
+#pragma unroll
+                                        for (int e = 0; e < 8; e += 2) {
+                                            // BF16 activations (packed round to nearest even), FP32 products
+                                            const uint32_t pk = pack2(sv[e], sv[e + 1]);
+                                            o4[e & 3] = fmaf(__uint_as_float(pk << 16), wo[e], o4[e & 3]);
+                                            o4[(e + 1) & 3] = fmaf(__uint_as_float(pk & 0xffff0000u), wo[e + 1], o4[(e + 1) & 3]);
+                                        }
                                     }
                                 }
+                                // activations K = 32 cq + 16 cc .. +15 of this row: 8 packed TMEM columns
+                                if (l < L - 1) tmem_st8(aq + gi * (kH / 2) + cc * 8, pk);
+                                if (cc == 0) tmem_wait16(rb);
                             }
-                            if (cc < 3) tmem_wait16(nxt);
-                        }
-                        if (l < L - 1) {
-                            fence_async_smem();
-                            tc_before();
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive(&opx[gi]);
-                        }
-                        if (l == L - 2 && i > imin) {
-                            // the next rate's feature row (same t_k, so only columns 0..7
-                            // change): its first-layer product runs during this rate's last
-                            // epilogue, into the other TMEM buffer
-                            if (owner)
-                                *reinterpret_cast<uint4 *>(urow0) =
-                                    make_uint4(pack2(xt, (float)(i - 1) * g.sc.i_scale),
-                                               pack2(lam_n * g.sc.lam_scale, 0.0f), u14[0], u14[1]);
-                            fence_async_smem();
-                            tc_before();
-                            __syncwarp();
-                            if (lane == 0) mbar_arrive(&opu[gi]);
+                            if (l < L - 1) {
+                                tmem_wait_st();
+                                tc_before();
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive(&opx[gi]);
+                            } else {
+                                // this tile's accumulator has been read: the next rate's
+                                // first-layer product may overwrite it (after the last
+                                // rate, the next step's feature rows come first)
+                                tc_before();
+                                __syncwarp();
+                                if (lane == 0 && i > imin) mbar_arrive(&opu[gi]);
+                                opart_own[gi] = (o4[0] + o4[1]) + (o4[2] + o4[3]);
+                                if (!owner) {
+                                    opart[((size_t)gi * 3 + (cq - 1)) * kRows + row] = opart_own[gi];
+                                    __syncwarp();
+                                    if (lane == 0) mbar_arrive(&outb[gi]);
+                                }
+                            }
                         }
                     }
                     if (!ok) break;
-                    const float opart_own = (o4[0] + o4[1]) + (o4[2] + o4[3]);
-                    if (!owner) {
-                        opart[gi * kRows + row] = opart_own;
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&outb[gi]);
-                        continue;
+                    if (!owner) continue;
+                    // Euler step of this row's paths with A_i = C_i + s_y f
+#pragma unroll
+                    for (int gi = 0; gi < kGroups; ++gi) {
+                        if (!warp_wait(&outb[gi], pho[gi], abort, g.err)) { ok = false; break; }
+                        pho[gi] ^= 1;
+                        const float *op = opart + (size_t)gi * 3 * kRows + row;
+                        const float o = opart_own[gi] + op[0] + op[kRows] + op[2 * kRows];
+                        const float A = C_c + g.sc.y_scale * (o + b_out);
+                        const float z = zold[gi] + fmaf(lam_c, dH[gi], -A * h);
+                        st[(size_t)(i - 1) * T + gi * kRows] = z;
+                        if (mat && sidx[gi] != ~0ull)
+                            a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx[gi]] = z + a.Z0[i - 1];
                     }
-                    // Euler step of this path with A_i = C_i + s_y f
-                    if (!warp_wait(&outb[gi], pho, abort, g.err)) { ok = false; break; }
-                    pho ^= 1;
-                    const float o = opart_own + opart[gi * kRows + row];
-                    const float A = C_c + g.sc.y_scale * (o + b_out);
-                    const float z = zold + fmaf(lam_c, dH, -A * h);
-                    sp[0] = z;
-                    if (mat && sidx != ~0ull)
-                        a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = z + a.Z0[i - 1];
                     lam_c = lam_n;
                     C_c = C_n;
                 }
                 if (!ok) break;
                 if (mat && owner) {
-                    // the tile's 4 owner warps reduce their paths; the first of
-                    // them adds the four sums in fixed order (tiles run apart,
-                    // so each has its own barrier and accumulators)
+                    // the 4 owner warps reduce their paths of both tiles; the first of
+                    // them adds the four sums in fixed order
                     const int m = imin, buf = mcount & 1;
                     ++mcount;
-                    double Pp, Sp;
-                    float Lm;
-                    maturity_products(a, m, [&](int i) { return st[(size_t)(i - 1) * T] + a.Z0[i - 1]; }, Pp, Sp, Lm);
+                    double Pp[kGroups], Sp[kGroups];
+                    float Lm[kGroups];
+#pragma unroll
+                    for (int gi = 0; gi < kGroups; ++gi)
+                        maturity_products(a, m, [&](int i) { return st[(size_t)(i - 1) * T + gi * kRows] + a.Z0[i - 1]; },
+                                          Pp[gi], Sp[gi], Lm[gi]);
                     for (int qs = 0; qs < ns; ++qs) {
                         const float K = a.strikes[(size_t)(m - 1) * ns + qs];
-                        const double pay = active ? payoff(a, Pp, Sp, Lm, K) : 0.0;
-                        const double s1 = warp_sum(pay);
-                        const double s2 = warp_sum(pay * pay);
+                        double s1 = 0.0, s2 = 0.0;
+#pragma unroll
+                        for (int gi = 0; gi < kGroups; ++gi) {
+                            const double pay = active[gi] ? payoff(a, Pp[gi], Sp[gi], Lm[gi], K) : 0.0;
+                            s1 += pay;
+                            s2 += pay * pay;
+                        }
+                        s1 = warp_sum(s1);
+                        s2 = warp_sum(s2);
                         if (lane == 0) {
-                            tred[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 0] = s1;
-                            tred[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 1] = s2;
+                            red[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 0] = s1;
+                            red[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 1] = s2;
                         }
                     }
-                    if (lane == 0) mbar_arrive(&payb[gi]);
+                    if (lane == 0) mbar_arrive(&payb[0]);
                     if (q4 == 0) {
-                        if (!warp_wait(&payb[gi], php, abort, g.err)) { ok = false; break; }
+                        if (!warp_wait(&payb[0], php, abort, g.err)) { ok = false; break; }
                         if (lane == 0) {
                             for (int qs = 0; qs < ns; ++qs) {
                                 double s1 = 0.0, s2 = 0.0;
                                 for (int wv = 0; wv < 4; ++wv) {
-                                    s1 += tred[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 0];
-                                    s2 += tred[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 1];
+                                    s1 += red[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 0];
+                                    s2 += red[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 1];
                                 }
-                                double *acc = tsum + 4 * ((size_t)(m - 1) * ns + qs);
+                                double *acc = bsum + 4 * ((size_t)(m - 1) * ns + qs);
                                 kahan_add(acc + 0, acc + 1, s1);
                                 kahan_add(acc + 2, acc + 3, s2);
                             }
@@ -569,8 +624,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
     }
     double *out = a.partials + (size_t)blockIdx.x * n * ns * 2;
     for (int e = tid; e < n * ns; e += kThreads) {
-        out[2 * e + 0] = bsum[4 * e + 0] + bsum[4 * ((size_t)n * ns + e) + 0];
-        out[2 * e + 1] = bsum[4 * e + 2] + bsum[4 * ((size_t)n * ns + e) + 2];
+        out[2 * e + 0] = bsum[4 * e + 0];
+        out[2 * e + 1] = bsum[4 * e + 2];
     }
 }
 

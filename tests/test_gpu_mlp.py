@@ -165,9 +165,12 @@ def test_mlp_scheme_against_fp64_oracle(lll, trained):
 def test_tcgen05_kernel_matches_mma_sync_kernel(lll, trained):
     """The tensor-memory kernel and the warp-level kernel evaluate the same
     network on the same paths: BF16 activations, FP32 accumulation in a
-    different order.  A rounding difference moves one activation by at most
-    2^-8 relative, which moves a drift by a small fraction of s_y; over the
-    312 steps the log-rates then agree to 2e-6 and the prices to 1e-9."""
+    different order (the tensor-memory kernel adds the rate's own inputs
+    t, i, lambda_i to the first layer through a per-rate bias).  A rounding
+    difference moves one activation by at most 2^-8 relative, which moves a
+    drift by a small fraction of s_y; over the 312 steps the log-rates then
+    agree to 2e-6.  A log-rate difference eps moves a caplet payoff by at most
+    delta B(0,T_N) L (1 + delta L)^n eps < 1e-2 eps, so the prices agree to 2e-8."""
     wl, x, W, sim, loss = trained
     cnt = 4096
     try:
@@ -186,8 +189,8 @@ def test_tcgen05_kernel_matches_mma_sync_kernel(lll, trained):
         lll.lll_mlp_set_kernel(sim.ctx, "auto")
     mask = ~np.isnan(z_w)
     assert np.abs(z_t[mask] - z_w[mask]).max() <= 2e-6
-    assert np.abs(p_t - p_w).max() <= 1e-9
-    assert np.abs(p_tr - p_wr).max() <= 1e-9
+    assert np.abs(p_t - p_w).max() <= 2e-8
+    assert np.abs(p_tr - p_wr).max() <= 2e-8
 
 
 @pytest.fixture(scope="module")
@@ -247,8 +250,8 @@ def test_layered_path_matches_fused_kernel(lll, trained):
         lll.lll_mlp_set_kernel(sim.ctx, "auto")
     mask = ~np.isnan(z_t)
     assert np.abs(z_l[mask] - z_t[mask]).max() <= 2e-6
-    assert np.abs(p_l - p_t).max() <= 1e-9
-    assert np.abs(p_lr - p_tr).max() <= 1e-9
+    assert np.abs(p_l - p_t).max() <= 2e-8  # bound of the test above
+    assert np.abs(p_lr - p_tr).max() <= 2e-8
 
 
 def test_wide_network_on_long_dated_workload_matches_fp64_scheme(lll):
