@@ -244,7 +244,7 @@ __device__ __forceinline__ void kahan_add(double *s, double *c, double x)
 
 // Shared-memory plan; operand tiles first (1024-byte aligned).
 struct TcLayout {
-    uint32_t w0, w, u, bias, w0c, hbw, wout, bars, misc, opart, red, bsum, total;
+    uint32_t w0, w, u, bias, w0c, hbw, wout, bars, misc, opart, red, bsum, state, lc, total;
 };
 
 __host__ __device__ inline TcLayout tc_layout(int L, int KB0, int n, int ns)
@@ -262,8 +262,10 @@ __host__ __device__ inline TcLayout tc_layout(int L, int KB0, int n, int ns)
     t.misc = o; o += 16;                          // TMEM base, abort word
     t.opart = o; o += kGroups * 3 * kRows * 4;    // output partials of column quarters 1..3, per tile
     o = (o + 15) & ~15u;
-    t.red = o; o += kGroups * 2 * 4 * ns * 2 * 8; // per tile: 4 owner warps' payoff sums, two buffers
-    t.bsum = o; o += kGroups * n * ns * 4 * 8;    // per tile: Kahan accumulators
+    t.red = o; o += 2 * 4 * ns * 2 * 8;           // 4 owner warps' payoff sums, two buffers
+    t.bsum = o; o += n * ns * 4 * 8;              // Kahan accumulators
+    t.state = o; o += n * kGroups * kRows * 4;    // log-rate offsets of the CTA's paths, [rate][path]
+    t.lc = o; o += kEpiWarps * 2 * ((n + 31) & ~31) * 4; // per warp: lambda_i(t_k) and C_i(t_k) of the step
     t.total = o + 1024;                           // slack for aligning the base
     return t;
 }
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
     for (int e = tid; e < kH; e += kThreads) wout[e] = __bfloat162float(g.wh[g.off_wout + e]);
     for (int e = tid; e < 3 * kH; e += kThreads)
         w0c[e] = 0.5f * __bfloat162float(g.wh[g.offW[0] + (size_t)(e % kH) * g.in_pad + e / kH]);
-    for (int e = tid; e < kGroups * 4 * n * ns; e += kThreads) bsum[e] = 0.0;
+    for (int e = tid; e < 4 * n * ns; e += kThreads) bsum[e] = 0.0;
     if (tid == 0) {
         for (int gi = 0; gi < kGroups; ++gi) {
             mbar_init(&opu[gi], kEpiWarps); // every epilogue warp
@@ -408,7 +410,9 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
         const uint32_t dq = tmem + ((uint32_t)(q4 * 32) << 16) + cq * 32;          // + tile * kH: accumulator
         const uint32_t aq = tmem + ((uint32_t)(q4 * 32) << 16) + 2 * kH + cq * 16; // + tile * kH / 2: activations
         float *hbw = reinterpret_cast<float *>(sm + lay.hbw) + warp * 32;
-        float *st = a.state + (size_t)blockIdx.x * n * T + row; // + tile * kRows
+        float *st = reinterpret_cast<float *>(sm + lay.state) + row; // [rate][path]: + (i - 1) T + tile * kRows
+        const int npad = (n + 31) & ~31;
+        float *lw = reinterpret_cast<float *>(sm + lay.lc) + (size_t)warp * 2 * npad; // lambda_i, then C_i
         const float h = a.h;
         const float b_out = g.wp[g.off_bout];
         uint32_t phd[kGroups] = {0, 0}, pho[kGroups] = {0, 0}, php = 0;
@@ -455,8 +459,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                         }
                     }
                 }
-                float lam_c = a.row[(size_t)k * n + (n - 1)].x, C_c = 0.0f; // every warp: lambda_i enters the bias
-                if (owner) C_c = g.Ctab[(size_t)k * n + (n - 1)];
+                // the step's lambda_i(t_k) (every warp: it enters the bias) and C_i(t_k)
+                for (int j = lane; j < n; j += 32) {
+                    lw[j] = a.row[(size_t)k * n + j].x;
+                    lw[npad + j] = g.Ctab[(size_t)k * n + j];
+                }
+                __syncwarp();
                 // feature rows written and (after the previous step's last rate) the
                 // accumulators free: the first rate's first-layer products may start
                 fence_async_smem();
@@ -466,15 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                     for (int gi = 0; gi < kGroups; ++gi) mbar_arrive(&opu[gi]);
                 const float xt_b = bf16_round(xt);
                 for (int i = n; ok && i >= imin; --i) {
-                    const size_t rowk = (size_t)k * n + (i - 1);
-                    float zold[kGroups] = {0.0f, 0.0f};
-                    float lam_n = 0.0f, C_n = 0.0f;
-                    if (i > imin) lam_n = a.row[rowk - 1].x;
-                    if (owner) {
-#pragma unroll
-                        for (int gi = 0; gi < kGroups; ++gi) zold[gi] = st[(size_t)(i - 1) * T + gi * kRows];
-                        if (i > imin) C_n = g.Ctab[rowk - 1];
-                    }
+                    const float lam_c = lw[i - 1];
                     {
                         // half first-layer bias of rate i for this warp's 32 columns:
                         // (b_0 + W_0[:, t] t + W_0[:, i] i + W_0[:, lambda] lambda_i) / 2,
@@ -558,14 +558,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                         pho[gi] ^= 1;
                         const float *op = opart + (size_t)gi * 3 * kRows + row;
                         const float o = opart_own[gi] + op[0] + op[kRows] + op[2 * kRows];
-                        const float A = C_c + g.sc.y_scale * (o + b_out);
-                        const float z = zold[gi] + fmaf(lam_c, dH[gi], -A * h);
+                        const float A = lw[npad + i - 1] + g.sc.y_scale * (o + b_out);
+                        const float z = st[(size_t)(i - 1) * T + gi * kRows] + fmaf(lam_c, dH[gi], -A * h);
                         st[(size_t)(i - 1) * T + gi * kRows] = z;
                         if (mat && sidx[gi] != ~0ull)
                             a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx[gi]] = z + a.Z0[i - 1];
                     }
-                    lam_c = lam_n;
-                    C_c = C_n;
                 }
                 if (!ok) break;
                 if (mat && owner) {
