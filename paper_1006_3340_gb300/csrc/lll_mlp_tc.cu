@@ -101,9 +101,21 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b)
 // Wait for the completion of the phase of parity `par`.  Gives up when the
 // CTA's abort word is set or after kWaitBudget cycles (then sets it, and the
 // launch's error word).
+__device__ __forceinline__ uint32_t mbar_test(uint32_t a, uint32_t par)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}\n"
+                 : "=r"(ok)
+                 : "r"(a), "r"(par)
+                 : "memory");
+    return ok;
+}
+
 __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t par, volatile int *abort, int *err)
 {
     const uint32_t a = saddr(b);
+    if (mbar_test(a, par)) return true; // completed already: no clock read, no suspend
     const long long t0 = clock64();
     while (true) {
         uint32_t ok;
@@ -128,6 +140,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t par, volatile in
 __device__ __forceinline__ bool warp_wait(uint64_t *b, uint32_t par, volatile int *abort, int *err)
 {
     const uint32_t a = saddr(b);
+    if (__all_sync(0xffffffffu, mbar_test(a, par))) return true;
     const long long t0 = clock64();
     while (true) {
         uint32_t ok;
@@ -256,7 +269,7 @@ __host__ __device__ inline TcLayout tc_layout(int L, int KB0, int n, int ns)
     t.u = o; o += kGroups * KB0 * kTileBytes;     // feature rows, per tile (hidden activations live in TMEM)
     t.bias = o; o += L * kH * 4;                  // b_0 / 2 .. b_{L-1} / 2
     t.w0c = o; o += 3 * kH * 4;                   // W_0 columns of t, i, lambda, halved
-    t.hbw = o; o += kEpiWarps * 64 * 4;           // per warp: first-layer half bias of the current rate
+    t.hbw = o; o += kEpiWarps * 64 * 4;           // per warp: first-layer half biases of two rates
     t.wout = o; o += kH * 4;                      // output weights (BF16 values)
     t.bars = o; o += 12 * 8;                      // mbarriers
     t.misc = o; o += 16;                          // TMEM base, abort word
@@ -409,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
         const bool owner = cq == 0;
         const uint32_t dq = tmem + ((uint32_t)(q4 * 32) << 16) + cq * 32;          // + tile * kH: accumulator
         const uint32_t aq = tmem + ((uint32_t)(q4 * 32) << 16) + 2 * kH + cq * 16; // + tile * kH / 2: activations
-        float *hbw = reinterpret_cast<float *>(sm + lay.hbw) + warp * 32;
+        float *hbw = reinterpret_cast<float *>(sm + lay.hbw) + warp * 64; // two rate slots of 32
         float *st = reinterpret_cast<float *>(sm + lay.state) + row; // [rate][path]: + (i - 1) T + tile * kRows
         const int npad = (n + 31) & ~31;
         float *lw = reinterpret_cast<float *>(sm + lay.lc) + (size_t)warp * 2 * npad; // lambda_i, then C_i
@@ -473,19 +486,36 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                 if (lane == 0)
                     for (int gi = 0; gi < kGroups; ++gi) mbar_arrive(&opu[gi]);
                 const float xt_b = bf16_round(xt);
+                // half first-layer bias of rate r for this warp's 32 columns, into slot r & 1:
+                // (b_0 + W_0[:, t] t + W_0[:, i] r + W_0[:, lambda] lambda_r) / 2, the inputs
+                // rounded to BF16 as the feature row would hold them
+                auto rate_bias = [&](int r) {
+                    const float xi_b = bf16_round((float)r * g.sc.i_scale);
+                    const float xl_b = bf16_round(lw[r - 1] * g.sc.lam_scale);
+                    const int c = cq * 32 + lane;
+                    hbw[(r & 1) * 32 + lane] =
+                        fmaf(w0c[2 * kH + c], xl_b, fmaf(w0c[kH + c], xi_b, fmaf(w0c[c], xt_b, bias[c])));
+                    __syncwarp();
+                };
+                // Euler step of rate r for this row's path in tile gi with A_r = C_r + s_y f;
+                // the owner applies it one rate late, off the products' critical path
+                float pend_own[kGroups] = {0.0f, 0.0f};
+                auto euler = [&](int r, int gi) {
+                    if (!warp_wait(&outb[gi], pho[gi], abort, g.err)) return false;
+                    pho[gi] ^= 1;
+                    const float *op = opart + (size_t)gi * 3 * kRows + row;
+                    const float o = pend_own[gi] + op[0] + op[kRows] + op[2 * kRows];
+                    const float A = lw[npad + r - 1] + g.sc.y_scale * (o + b_out);
+                    float *sp = st + (size_t)(r - 1) * T + gi * kRows;
+                    const float z = sp[0] + fmaf(lw[r - 1], dH[gi], -A * h);
+                    sp[0] = z;
+                    if (mat && sidx[gi] != ~0ull)
+                        a.snap[((size_t)(imin - 1) * n + (r - 1)) * a.snap_pitch + sidx[gi]] = z + a.Z0[r - 1];
+                    return true;
+                };
+                rate_bias(n);
                 for (int i = n; ok && i >= imin; --i) {
-                    const float lam_c = lw[i - 1];
-                    {
-                        // half first-layer bias of rate i for this warp's 32 columns:
-                        // (b_0 + W_0[:, t] t + W_0[:, i] i + W_0[:, lambda] lambda_i) / 2,
-                        // the inputs rounded to BF16 as the feature row would hold them
-                        const float xi_b = bf16_round((float)i * g.sc.i_scale);
-                        const float xl_b = bf16_round(lam_c * g.sc.lam_scale);
-                        const int c = cq * 32 + lane;
-                        hbw[lane] = fmaf(w0c[2 * kH + c], xl_b, fmaf(w0c[kH + c], xi_b, fmaf(w0c[c], xt_b, bias[c])));
-                        __syncwarp();
-                    }
-                    float opart_own[kGroups] = {0.0f, 0.0f};
+                    const float *hb0 = hbw + (i & 1) * 32;
 #pragma unroll
                     for (int l = 0; l < L; ++l) {
 #pragma unroll
@@ -495,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                             phd[gi] ^= 1;
                             tc_after();
                             const uint32_t dbuf = dq + gi * kH;
-                            const float *hbl = l == 0 ? hbw : bias + l * kH + cq * 32;
+                            const float *hbl = l == 0 ? hb0 : bias + l * kH + cq * 32;
                             float o4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                             uint32_t ra[16], rb[16];
                             tmem_ld16(dbuf, ra);
@@ -532,7 +562,15 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                                 tmem_wait_st();
                                 tc_before();
                                 __syncwarp();
+                                // the previous rate's Euler step: its output partials can be
+                                // overwritten only after this warp's next arrival on opx, or,
+                                // with one hidden product per rate, after this one
+                                if (l == 0 && owner && i < n && L == 2)
+                                    if (!euler(i + 1, gi)) { ok = false; continue; }
                                 if (lane == 0) mbar_arrive(&opx[gi]);
+                                if (l == 0 && owner && i < n && L > 2)
+                                    if (!euler(i + 1, gi)) { ok = false; continue; }
+                                if (l == 0 && gi == kGroups - 1 && i > imin) rate_bias(i - 1);
                             } else {
                                 // this tile's accumulator has been read: the next rate's
                                 // first-layer product may overwrite it (after the last
@@ -540,31 +578,22 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                                 tc_before();
                                 __syncwarp();
                                 if (lane == 0 && i > imin) mbar_arrive(&opu[gi]);
-                                opart_own[gi] = (o4[0] + o4[1]) + (o4[2] + o4[3]);
-                                if (!owner) {
-                                    opart[((size_t)gi * 3 + (cq - 1)) * kRows + row] = opart_own[gi];
+                                const float part = (o4[0] + o4[1]) + (o4[2] + o4[3]);
+                                if (owner) {
+                                    pend_own[gi] = part;
+                                } else {
+                                    opart[((size_t)gi * 3 + (cq - 1)) * kRows + row] = part;
                                     __syncwarp();
                                     if (lane == 0) mbar_arrive(&outb[gi]);
                                 }
                             }
                         }
                     }
-                    if (!ok) break;
-                    if (!owner) continue;
-                    // Euler step of this row's paths with A_i = C_i + s_y f
-#pragma unroll
-                    for (int gi = 0; gi < kGroups; ++gi) {
-                        if (!warp_wait(&outb[gi], pho[gi], abort, g.err)) { ok = false; break; }
-                        pho[gi] ^= 1;
-                        const float *op = opart + (size_t)gi * 3 * kRows + row;
-                        const float o = opart_own[gi] + op[0] + op[kRows] + op[2 * kRows];
-                        const float A = lw[npad + i - 1] + g.sc.y_scale * (o + b_out);
-                        const float z = st[(size_t)(i - 1) * T + gi * kRows] + fmaf(lam_c, dH[gi], -A * h);
-                        st[(size_t)(i - 1) * T + gi * kRows] = z;
-                        if (mat && sidx[gi] != ~0ull)
-                            a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx[gi]] = z + a.Z0[i - 1];
-                    }
                 }
+                // the step's last rate
+                if (owner)
+                    for (int gi = 0; ok && gi < kGroups; ++gi)
+                        if (!euler(imin, gi)) ok = false;
                 if (!ok) break;
                 if (mat && owner) {
                     // the 4 owner warps reduce their paths of both tiles; the first of
