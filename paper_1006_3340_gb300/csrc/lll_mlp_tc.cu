@@ -226,13 +226,17 @@ __device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16])
 // Bias + SiLU of 8 accumulator values: with z = v + b and hz = z / 2 (from
 // the half bias hb), SiLU(z) = z sigma(z) = hz + hz tanh(hz), the same
 // function as the training kernels' z (1 + tanh(z / 2)) / 2 (one MUFU
-// operation and two f32x2 FMAs per pair).
+// operation and two f32x2 FMAs per pair).  hb is 16-byte aligned: the eight
+// biases come in two 128-bit shared loads (one wavefront each, all lanes
+// reading the same address).
 __device__ __forceinline__ void silu8(const uint32_t *v, const float *hb, float (&sv)[8])
 {
+    const float4 b0 = *reinterpret_cast<const float4 *>(hb), b1 = *reinterpret_cast<const float4 *>(hb + 4);
+    const float hbv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
     for (int e = 0; e < 8; e += 2) {
         const float2 hz = __ffma2_rn(make_float2(__uint_as_float(v[e]), __uint_as_float(v[e + 1])),
-                                     make_float2(0.5f, 0.5f), make_float2(hb[e], hb[e + 1]));
+                                     make_float2(0.5f, 0.5f), make_float2(hbv[e], hbv[e + 1]));
         const float2 t = make_float2(tanh_approx(hz.x), tanh_approx(hz.y));
         const float2 r = __ffma2_rn(hz, t, hz);
         sv[e] = r.x;
@@ -544,7 +548,9 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
 #pragma unroll
                                         for (int e = 0; e < 4; ++e) pk[qd * 4 + e] = pack2(sv[2 * e], sv[2 * e + 1]);
                                     } else {
-                                        const float *wo = wout + cq * 32 + cc * 16 + qd * 8;
+                                        const float4 w0 = *reinterpret_cast<const float4 *>(wout + cq * 32 + cc * 16 + qd * 8);
+                                        const float4 w1 = *reinterpret_cast<const float4 *>(wout + cq * 32 + cc * 16 + qd * 8 + 4);
+                                        const float wo[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
                                         for (int e = 0; e < 8; e += 2) {
                                             // BF16 activations (packed round to nearest even), FP32 products
