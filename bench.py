@@ -192,6 +192,147 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """The batched configuration: 256 independent term structures of uneven tenor
+    count, strike grid and path budget (2^24 paths in total) in one persistent
+    launch per scheme, replayed as a CUDA graph.  One step = the Picard and the
+    full scheme over every instance.  Single GPU."""
+    import torch
+
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        print(json.dumps({"error": "--workload batch256 runs on one GPU"}), flush=True)
+        return 1
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_1006_3340_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1006_3340_gb300 import autotune, lll
+
+    wls = workloads.batched_instances()
+    schemes = [s for s in args.schemes.split(",") if s in ("picard", "full")] or ["picard", "full"]
+    inst = []
+    for wl in wls:
+        x, W = lll.lll_build_nig_quadrature(wl.alpha, wl.beta, wl.dbar, wl.a, wl.Q)
+        inst.append((wl, x, W))
+    units = sum(wl.paths * wl.units_per_path() for wl in wls)          # per scheme
+    lane_ops = sum(wl.paths * wl.units_per_path() * 3 * wl.Q for wl in wls)
+    caplets = sum(wl.n * wl.strikes.shape[1] for wl in wls)
+    b, keep = lll.lll_batch_init(inst)  # default stream, the one torch's events record on
+    tuned = autotune.tune_batch(b, inst, "full")  # one launch shape for both schemes
+    lll.lll_batch_use_graph(b, True)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def one_step(evs=None):
+        for i, s in enumerate(schemes):
+            if evs is not None:
+                evs[i][0].record()
+            lll.lll_batch_simulate(b, lll.SCHEMES[s], 42)
+            if evs is not None:
+                evs[i][1].record()
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(0.3)
+    per_ms = {s: [] for s in schemes}
+    kernel_ms = {s: [] for s in schemes}
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)  # L2 flush between timed steps (outside the events)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in schemes]
+        for i, s in enumerate(schemes):
+            evs[i][0].record()
+            lll.lll_batch_simulate(b, lll.SCHEMES[s], 42)
+            evs[i][1].record()
+            torch.cuda.synchronize()
+            kernel_ms[s].append(lll.lll_batch_kernel_ms(b))
+        for i, s in enumerate(schemes):
+            per_ms[s].append(evs[i][0].elapsed_time(evs[i][1]))
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_ms = sum(sum(v) for v in per_ms.values())
+    value = units * len(schemes) * args.steps / (total_ms * 1e-3)
+    per = {}
+    for s in schemes:
+        ms = statistics.mean(per_ms[s])
+        p0, _ = lll.lll_batch_prices(b, 0, wls[0].n, wls[0].strikes.shape[1])
+        per[s] = {"units_per_s": units / (ms * 1e-3), "ms": ms, "batch_kernel_ms": statistics.mean(kernel_ms[s]),
+                  "caplets_per_s": caplets / (ms * 1e-3), "inst0_atm_first_maturity": float(p0[0, 5])}
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = sms * 128 * sm_max * 1e6 / 1e12
+    dom = max(schemes, key=lambda s: statistics.mean(kernel_ms[s]))
+    ach = lane_ops / (statistics.mean(kernel_ms[dom]) * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFP32-lane-op/s",
+                "frac": ach / fp32_peak, "traffic": None,
+                "kernel": f"batch_kernel ({dom}), 3Q FP32 lane-ops per unit, Q=64",
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS)"}
+
+    # end to end through the C ABI from host arrays: batch init (instance inputs
+    # host to device, FP64 tables), both schemes, every instance's prices back
+    e2e = None
+    if not args.no_e2e:
+        h2d = sum(wl.L0.nbytes + wl.lam.nbytes + x.nbytes + W.nbytes + wl.strikes.nbytes for wl, x, W in inst)
+        d2h = len(schemes) * sum(2 * 8 * wl.n * wl.strikes.shape[1] for wl in wls)
+        ts = []
+        for _ in range(max(2, args.steps)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b2, keep2 = lll.lll_batch_init(inst)
+            lll.lll_batch_set_launch(b2, *tuned["launch"])
+            for s in schemes:
+                lll.lll_batch_simulate(b2, lll.SCHEMES[s], 42)
+                for q, wl in enumerate(wls):
+                    lll.lll_batch_prices(b2, q, wl.n, wl.strikes.shape[1])
+            lll.lll_batch_destroy(b2)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        et = statistics.mean(ts)
+        e2e = {"value": units * len(schemes) / et, "unit": "path·tenor·steps/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "caplets_per_s": caplets * len(schemes) / et,
+               "note": "lll_batch_init (tables built on the GPU) + lll_batch_simulate per scheme + "
+                       "lll_batch_prices of every instance + lll_batch_destroy"}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as ora
+        from oracle import quadrature
+        threads = os.cpu_count() or 1
+        codes = {"picard": ora.PICARD, "full": ora.FULL}
+        done_units, t0, q = 0, time.perf_counter(), 0
+        while time.perf_counter() - t0 < 12.0 and q < len(wls):
+            wl = wls[q]
+            xq, Wq = quadrature.rule_for(wl)
+            model = ora.OracleModel(wl, xq, Wq)
+            npaths = min(wl.paths, 512)
+            for s in schemes:
+                ora.simulate(model, codes[s], npaths=npaths, threads=threads, seed=42, inst=q)
+                done_units += npaths * wl.units_per_path()
+            q += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": done_units / dt, "unit": "path·tenor·steps/s", "cores": threads, "kind": "oracle",
+               "sample": f"instances 0..{q - 1}, first min(paths, 512) paths each, {'+'.join(schemes)}; "
+                         f"FP64 C oracle, {threads} threads, {dt:.1f} s"}
+
+    line = {"metric": METRIC, "value": value, "unit": "path·tenor·steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch256: {len(wls)} uneven term structures (N 8..80, delta 0.25/0.5), "
+                                   f"{sum(wl.paths for wl in wls)} paths in total, 11 strikes, "
+                                   f"schemes={'+'.join(schemes)}, one persistent launch per scheme (CUDA graph)",
+                       "global_paths": sum(wl.paths for wl in wls), "parallelism": "one GPU",
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write outside the events)"},
+            "per_scheme": per, "caplets_per_s": caplets * len(schemes) * args.steps / (total_ms * 1e-3),
+            "roofline": roofline, "autotuned": tuned, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": 2 * len(schemes) * args.steps}
+    print(json.dumps(line), flush=True)
+    lll.lll_batch_destroy(b)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -208,9 +349,14 @@ def main():
                     help="LLL_MLP kernel: tcgen05/TMEM (tc), mma.sync (warp) or the library's choice")
     ap.add_argument("--launch", default="", help="fixed launch shape for the quadrature schemes: "
                     "threads,blocks_per_sm,chunk_rows,paths_per_thread,lanes_per_path (no tuning)")
+    ap.add_argument("--workload", default="large_single", choices=["large_single", "batch256"],
+                    help="large_single: the N=40 term structure (default); batch256: 256 uneven term "
+                    "structures in one launch per scheme (Picard and full only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch256":
+        return run_batch(args)
 
     import torch
     import torch.distributed as dist
@@ -336,7 +482,9 @@ def main():
         kms, _ = sims[s].kernel_ms()
         p, se = sims[s].prices()
         per[s] = {"units_per_s": wl.paths * wl.units_per_path() / (ms * 1e-3), "ms": ms,
-                  "path_kernel_ms_last": kms, "atm_price_T10y": float(p[n - 1, ns // 2])}
+                  "path_kernel_ms_last": kms, "atm_price_T10y": float(p[n - 1, ns // 2]),
+                  # one simulation prices every (maturity, strike) caplet of the term structure
+                  "caplets_per_s": n * ns / (ms * 1e-3)}
     if "picard" in per and "full" in per:
         pp, _ = sims["picard"].prices()
         pf, _ = sims["full"].prices()
@@ -451,6 +599,7 @@ def main():
             et = float(t.item())
         e2e = {"value": units_per_step / et, "unit": "path·tenor·steps/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "caplets_per_s": len(schemes) * n * ns * world / et,
                "note": "per scheme: lll_init + lll_set_strikes (+ network parameters for mlp) + lll_simulate + lll_price_caplets + lll_destroy"}
 
     cpu = None
