@@ -35,8 +35,21 @@ L2_FLUSH_BYTES = 512 << 20
 
 
 def _workload(args):
-    wl = workloads.large_single(paths=args.paths or (1 << 20))
-    return wl
+    if getattr(args, "workload", "large_single") == "long_dated":
+        return workloads.long_dated(paths=args.paths or (1 << 22))
+    return workloads.large_single(paths=args.paths or (1 << 20))
+
+
+def _arch(wl):
+    """(hidden width, hidden layers) of the learned compensator for a workload:
+    43->128x3->1 on N=40, 123->256x4->1 on N=120."""
+    return (256, 4) if wl.N > 61 else (128, 3)
+
+
+def _schemes(args):
+    if args.schemes:
+        return [s for s in args.schemes.split(",") if s]
+    return ["picard", "full"] if args.workload == "long_dated" else ["picard", "full", "mlp"]
 
 
 def _code(s):
@@ -134,7 +147,7 @@ def cpu_baseline(wl, schemes, budget_s=12.0, threads=None):
     model = ora.OracleModel(wl, x, W)
     threads = threads or os.cpu_count() or 1
     codes = {"picard": ora.PICARD, "full": ora.FULL, "frozen": ora.FROZEN}
-    batch = 1024
+    batch = 1024 if wl.N <= 61 else 128  # the N=120 oracle costs about 30x more per path
     units = 0
     done = {s: 0 for s in schemes}
     t0 = time.perf_counter()
@@ -341,7 +354,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--paths", type=int, default=0, help="paths per GPU (default 2^20)")
     ap.add_argument("--ref-paths", type=int, default=512, help="oracle paths per scheme per step")
-    ap.add_argument("--schemes", default="picard,full,mlp")
+    ap.add_argument("--schemes", default="", help="default picard,full,mlp (large_single), picard,full (long_dated)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="library default launch shapes")
@@ -349,9 +362,10 @@ def main():
                     help="LLL_MLP kernel: tcgen05/TMEM (tc), mma.sync (warp) or the library's choice")
     ap.add_argument("--launch", default="", help="fixed launch shape for the quadrature schemes: "
                     "threads,blocks_per_sm,chunk_rows,paths_per_thread,lanes_per_path (no tuning)")
-    ap.add_argument("--workload", default="large_single", choices=["large_single", "batch256"],
-                    help="large_single: the N=40 term structure (default); batch256: 256 uneven term "
-                    "structures in one launch per scheme (Picard and full only)")
+    ap.add_argument("--workload", default="large_single", choices=["large_single", "long_dated", "batch256"],
+                    help="large_single: the N=40 term structure, 2^20 paths (default); long_dated: N=120, "
+                    "Q=96, 2^22 paths; batch256: 256 uneven term structures in one launch per scheme "
+                    "(Picard and full only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -374,7 +388,8 @@ def main():
     from paper_1006_3340_gb300 import lll
 
     wl = _workload(args)
-    schemes = [s for s in args.schemes.split(",") if s]
+    schemes = _schemes(args)
+    hid, lay = _arch(wl)
     n, ns = wl.n, wl.strikes.shape[1]
     first = rank * wl.paths
     stream = torch.cuda.current_stream(dev).cuda_stream
@@ -389,14 +404,14 @@ def main():
         # with the project's GPU kernels; the timed steps then price with it.
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        loss = lll.lll_mlp_train(sims["mlp"].ctx, hidden=128, layers=3, train_paths=1 << 16,
+        loss = lll.lll_mlp_train(sims["mlp"].ctx, hidden=hid, layers=lay, train_paths=1 << 16,
                                  records_per_path=8, epochs=4, batch=8192, lr=2e-3, lr_final=1e-4, seed=7)
         torch.cuda.synchronize()
         lll.lll_mlp_set_kernel(sims["mlp"].ctx, args.mlp_kernel)
-        n_params, in_dim, in_pad, _ = lll.lll_mlp_layout(sims["mlp"].ctx, 3)
+        n_params, in_dim, in_pad, _ = lll.lll_mlp_layout(sims["mlp"].ctx, lay)
         mlp_params = lll.lll_mlp_params(sims["mlp"].ctx, 0, count=n_params)
         mlp_info = {"train_s": time.perf_counter() - t0, "final_loss_scaled": loss, "params": int(n_params),
-                    "arch": f"{in_dim}->128x3->1 SiLU, BF16 weights, FP32 accumulate",
+                    "arch": f"{in_dim}->{hid}x{lay}->1 SiLU, BF16 weights, FP32 accumulate",
                     "train_pairs": "2^16 paths x 8 recorded steps x live rates (~1e7)"}
 
     if "mlp_vec" in schemes:
@@ -538,9 +553,9 @@ def main():
         ms = statistics.mean(per_scheme_ms[s])
         t = ms * 1e-3
         if s == "mlp":
-            in_pad = 48 if wl.N + 3 <= 48 else 64
-            flop = units * 2 * (in_pad * 128 + 128 * 128 * 2 + 128)  # per (path, rate, step) row
-            silu = units * 3 * 128
+            in_pad = 16 * ((wl.N + 3 + 15) // 16)
+            flop = units * 2 * (in_pad * hid + hid * hid * (lay - 1) + hid)  # per (path, rate, step) row
+            silu = units * lay * hid
         else:
             path_steps = wl.paths * wl.steps * world
             flop = path_steps * 2 * (48 * 128 + 128 * 128 * 2 + 128 * 48)  # one pass per (path, step)
@@ -555,7 +570,8 @@ def main():
                 "tensor_tflops": tflops, "tensor_frac": tflops / bf16,
                 "tensor_peak_basis": "bf16_tflops_sustained of MEASURED_PEAKS",
                 "traffic": _traffic(key) if (s == "mlp" and wl.paths == 1 << 20) else None,
-                "kernel": ("mlp path kernel (mma.sync bf16)" if s == "mlp" and (args.mlp_kernel == "warp" or wl.N + 3 > 64)
+                "kernel": ("mlp layered path (training GEMMs)" if s == "mlp" and hid != 128 else
+                           "mlp path kernel (mma.sync bf16)" if s == "mlp" and (args.mlp_kernel == "warp" or wl.N + 3 > 64)
                            else "mlp path kernel (tcgen05 bf16, TMEM accumulators)"
                            + (", vector head" if s == "mlp_vec" else ""))}
 
@@ -581,7 +597,7 @@ def main():
                 if s in tuned:
                     sim.set_launch(*tuned[s]["launch(threads,bps,chunk,ppt,lanes)"])
                 if s == "mlp":
-                    lll.lll_mlp_init(sim.ctx, 128, 3, 0)
+                    lll.lll_mlp_init(sim.ctx, hid, lay, 0)
                     lll.lll_mlp_params(sim.ctx, 1, mlp_params[0], scales=mlp_params[1])
                     lll.lll_mlp_set_kernel(sim.ctx, args.mlp_kernel)
                 if s == "mlp_vec":
