@@ -665,16 +665,20 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
 
 // ---------------------------------------------------------------------------
 // Vector head: one network pass per (path, Euler step) gives every rate's
-// compensator (output layer N = kOut columns, column i - 1 for rate i).  The
-// CTA layout is the per-rate kernel's (two tiles of 128 paths, two threads per
-// row, one MMA lane); per step a tile runs L hidden products and one output
-// product, then the row's owner applies all live rates' drifts.
+// compensator.  The CTA layout is the per-rate kernel's (two tiles of 128
+// paths, sixteen epilogue warps shared by both tiles, activations in TMEM, one
+// MMA lane).  W_out's rows are staged two columns down, so that output column c
+// belongs to rate c - 1, the rate whose log-rate sits in feature column c: the
+// warp of column quarter cq reads its 16 output columns, applies the Euler
+// step of those rates and writes their feature columns for the next step,
+// with no exchange between warps.
 // ---------------------------------------------------------------------------
-constexpr int kOut = 48;                       // output columns (n <= 48)
-constexpr int kOutBlock = kOut * 128;          // one 64-wide K block of W_out (48 rows)
+constexpr int kOut = 48;                       // network outputs (column i - 1 for rate i; n <= 48)
+constexpr int kOutN = 64;                      // output product width: columns 0 .. 63, rate c - 1
+constexpr int kOutBlock = kOutN * 128;         // one 64-wide K block of the staged W_out
 
 struct TcVecLayout {
-    uint32_t w0, w, wo, u, x, bias, bout, bars, misc, opart, red, bsum, total;
+    uint32_t w0, w, wo, u, bias, bout, bars, misc, red, bsum, state, lc, total;
 };
 
 __host__ __device__ inline TcVecLayout tc_vec_layout(int L, int KB0, int n, int ns)
@@ -683,19 +687,18 @@ __host__ __device__ inline TcVecLayout tc_vec_layout(int L, int KB0, int n, int 
     uint32_t o = 0;
     t.w0 = o; o += KB0 * kTileBytes;             // W_0: H rows x 64 KB0 columns
     t.w = o; o += (L - 1) * 2 * kTileBytes;       // W_1 .. W_{L-1}
-    t.wo = o; o += 2 * kOutBlock;                 // W_out: 48 rows x 128 columns
-    o = (o + 1023) & ~1023u;
+    t.wo = o; o += 2 * kOutBlock;                 // W_out staged: 64 rows x 128 columns
     t.u = o; o += kGroups * KB0 * kTileBytes;     // feature rows, per tile
-    t.x = o; o += kGroups * 2 * kTileBytes;       // hidden activations, per tile
     t.bias = o; o += L * kH * 4;                  // b_0 / 2 .. b_{L-1} / 2
-    t.bout = o; o += kOut * 4;                    // output biases
-    t.bars = o; o += 12 * 8;
-    t.misc = o; o += 16;
-    t.opart = o; o += 16;                         // (unused by the vector head)
+    t.bout = o; o += kOutN * 4;                   // output bias of column c (rate c - 1)
+    t.bars = o; o += 12 * 8;                      // mbarriers
+    t.misc = o; o += 16;                          // TMEM base, abort word
     o = (o + 15) & ~15u;
-    t.red = o; o += kGroups * 2 * 4 * ns * 2 * 8;
-    t.bsum = o; o += kGroups * n * ns * 4 * 8;
-    t.total = o + 1024;
+    t.red = o; o += 2 * 4 * ns * 2 * 8;           // 4 owner warps' payoff sums, two buffers
+    t.bsum = o; o += n * ns * 4 * 8;              // Kahan accumulators
+    t.state = o; o += n * kGroups * kRows * 4;    // log-rate offsets of the CTA's paths, [rate][path]
+    t.lc = o; o += kEpiWarps * 2 * 16 * 4;        // per warp: lambda and C of its 16 rates at t_k
+    t.total = o + 1024;                           // slack for aligning the base
     return t;
 }
 
@@ -711,38 +714,47 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
     float *bias = reinterpret_cast<float *>(sm + lay.bias);
     float *bout = reinterpret_cast<float *>(sm + lay.bout);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + lay.bars);
-    uint64_t *opu = bars + 0, *opx = bars + 2, *dnb = bars + 4, *payb = bars + 8, *finb = bars + 10;
+    uint64_t *opu = bars + 0;   // [kGroups] feature rows written, accumulator free (every epilogue warp)
+    uint64_t *opx = bars + 2;   // [kGroups] activations written (every epilogue warp)
+    uint64_t *dnb = bars + 4;   // [kGroups] product complete (commit)
+    uint64_t *eul = bars + 6;   // Euler steps of quarters 1..3 done, at a maturity (12 warps)
+    uint64_t *payb = bars + 7;  // payoff partials written (the 4 path-owning warps)
+    uint64_t *finb = bars + 8;  // all products complete (commit)
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + lay.misc);
     volatile int *abort = reinterpret_cast<volatile int *>(sm + lay.misc + 4);
     double *red = reinterpret_cast<double *>(sm + lay.red);
     double *bsum = reinterpret_cast<double *>(sm + lay.bsum);
     const int in_pad = g.in_pad;
 
-    // weights into the swizzled operand layout (W_out: rows 0 .. kOut - 1)
+    // weights into the swizzled operand layout; W_out row j (rate j + 1) goes to row j + 2
     for (int l = 0; l <= L; ++l) {
         const int din = l == 0 ? in_pad : kH;
-        const int rows = l == L ? kOut : kH;
+        const int rows = l == L ? kOutN : kH;
         const int chunks = l == 0 ? KB0 * 8 : 16;
-        const __nv_bfloat16 *W = g.wh + (l == L ? g.off_wout : g.offW[l]);
         const uint32_t base = l == 0 ? lay.w0 : (l == L ? lay.wo : lay.w + (l - 1) * 2 * kTileBytes);
         for (int e = tid; e < rows * chunks; e += kThreads) {
             const int h = e / chunks, c = e % chunks;
             uint4 v = make_uint4(0, 0, 0, 0);
-            if (c * 8 < din) v = *reinterpret_cast<const uint4 *>(W + (size_t)h * din + c * 8);
+            if (l < L) {
+                if (c * 8 < din) v = *reinterpret_cast<const uint4 *>(g.wh + g.offW[l] + (size_t)h * din + c * 8);
+            } else if (h >= 2 && h - 2 < kOut) {
+                v = *reinterpret_cast<const uint4 *>(g.wh + g.off_wout + (size_t)(h - 2) * din + c * 8);
+            }
             *reinterpret_cast<uint4 *>(sm + base + (c >> 3) * rows * 128 + (h >> 3) * 1024 + (h & 7) * 128 +
                                        (((c & 7) ^ (h & 7)) << 4)) = v;
         }
     }
     for (int e = tid; e < L * kH; e += kThreads) bias[e] = 0.5f * g.wp[g.offb[e / kH] + e % kH];
-    for (int e = tid; e < kOut; e += kThreads) bout[e] = g.wp[g.off_bout + e];
-    for (int e = tid; e < kGroups * 4 * n * ns; e += kThreads) bsum[e] = 0.0;
+    for (int e = tid; e < kOutN; e += kThreads) bout[e] = (e >= 2 && e - 2 < kOut) ? g.wp[g.off_bout + e - 2] : 0.0f;
+    for (int e = tid; e < 4 * n * ns; e += kThreads) bsum[e] = 0.0;
     if (tid == 0) {
         for (int gi = 0; gi < kGroups; ++gi) {
-            mbar_init(&opu[gi], 8);
-            mbar_init(&opx[gi], 8);
+            mbar_init(&opu[gi], kEpiWarps);
+            mbar_init(&opx[gi], kEpiWarps);
             mbar_init(&dnb[gi], 1);
-            mbar_init(&payb[gi], 4);
         }
+        mbar_init(eul, 12);
+        mbar_init(payb, 4);
         mbar_init(finb, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -750,200 +762,238 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
     fence_async_smem();
     if (warp == kEpiWarps) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(tslot)),
-                     "r"(kGroups * 2 * kH));
+                     "r"(4 * kH));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_before();
     __syncthreads();
     tc_after();
-    const uint32_t tmem = *tslot;
-    const uint64_t ntiles = (a.paths + kGroups * kRows - 1) / (kGroups * kRows);
+    const uint32_t tmem = *tslot; // accumulator of tile gi: columns [128 gi, +128); activations [256 + 64 gi, +64)
+    const int T = kGroups * kRows;
+    const uint64_t ntiles = (a.paths + T - 1) / T;
 
     if (warp == kEpiWarps) {
-        // MMA issuer: per step and tile, L hidden products and the output product
-        // (job j into TMEM buffer j & 1 of the tile), tiles in turn
+        // MMA issuer: per step and tile, the first layer (feature rows), the
+        // hidden layers and the output product (activations in TMEM), tiles in turn
         if (lane == 0) {
-            uint32_t phu[kGroups] = {0, 0}, phx[kGroups] = {0, 0};
-            uint64_t job = 0;
+            uint32_t phu = 0, phx = 0; // bit gi: phase parity of opu[gi], opx[gi]
             bool ok = !g.stall_mma;
-            for (uint64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-                for (int k = 0; ok && k < S; ++k) {
-                    for (int l = 0; ok && l <= L; ++l, ++job) {
+            for (uint64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x)
+                for (int k = 0; ok && k < S; ++k)
+                    for (int l = 0; ok && l <= L; ++l)
                         for (int gi = 0; gi < kGroups; ++gi) {
                             uint64_t *ob = l == 0 ? &opu[gi] : &opx[gi];
-                            uint32_t &ph = l == 0 ? phu[gi] : phx[gi];
-                            if (!mbar_wait(ob, ph, abort, g.err)) { ok = false; break; }
-                            ph ^= 1;
+                            uint32_t &ph = l == 0 ? phu : phx;
+                            if (!mbar_wait(ob, (ph >> gi) & 1u, abort, g.err)) { ok = false; break; }
+                            ph ^= 1u << gi;
                             tc_after();
-                            const uint32_t d = tmem + gi * 2 * kH + (uint32_t)(job & 1) * kH;
-                            const uint32_t abase = sbase + (l == 0 ? lay.u + gi * KB0 * kTileBytes
-                                                                   : lay.x + gi * 2 * kTileBytes);
-                            const uint32_t bbase =
-                                sbase + (l == 0 ? lay.w0 : (l == L ? lay.wo : lay.w + (l - 1) * 2 * kTileBytes));
-                            const uint32_t bstride = l == L ? (uint32_t)kOutBlock : (uint32_t)kTileBytes;
-                            const uint32_t id = l == L ? idesc_n(kOut) : kIdesc;
-                            const int ks_n = l == 0 ? in_pad / 16 : kH / 16;
-                            for (int ks = 0; ks < ks_n; ++ks) {
-                                const uint32_t ao = (ks >> 2) * kTileBytes + (ks & 3) * 32;
-                                const uint32_t bo = (ks >> 2) * bstride + (ks & 3) * 32;
-                                mma_bf16_id(d, sdesc(abase + ao), sdesc(bbase + bo), id, ks > 0);
+                            const uint32_t d = tmem + gi * kH;
+                            if (l == 0) {
+                                const uint32_t abase = sbase + lay.u + gi * KB0 * kTileBytes;
+                                for (int ks = 0; ks < in_pad / 16; ++ks) {
+                                    const uint32_t off = (ks >> 2) * kTileBytes + (ks & 3) * 32;
+                                    mma_bf16(d, sdesc(abase + off), sdesc(sbase + lay.w0 + off), ks > 0);
+                                }
+                            } else {
+                                const uint32_t at = tmem + 2 * kH + gi * (kH / 2);
+                                const uint32_t bbase = sbase + (l == L ? lay.wo : lay.w + (l - 1) * 2 * kTileBytes);
+                                const uint32_t bstride = l == L ? (uint32_t)kOutBlock : (uint32_t)kTileBytes;
+                                const uint32_t id = l == L ? idesc_n(kOutN) : kIdesc;
+                                for (int ks = 0; ks < kH / 16; ++ks) {
+                                    const uint32_t bo = (ks >> 2) * bstride + (ks & 3) * 32;
+                                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n"
+                                                 ::"r"(d), "r"(at + ks * 8), "l"(sdesc(bbase + bo)), "r"(id),
+                                                 "r"((uint32_t)(ks > 0)));
+                                }
                             }
                             mma_commit(&dnb[gi]);
                         }
-                    }
-                }
-            }
             mma_commit(finb);
             volatile int dummy_abort = 0;
             mbar_wait(finb, 0, &dummy_abort, g.err);
         }
         __syncwarp();
     } else {
-        const int gi = warp >> 3, hf = (warp >> 2) & 1, q4 = warp & 3;
+        // warp = 4 cq + q4: TMEM lane quadrant q4 (row 32 q4 + lane of each tile) and
+        // column quarter cq: columns 32 cq .. +31 of the hidden layers, output and
+        // feature columns 16 cq .. +15, that is rates 16 cq - 1 .. 16 cq + 14.
+        const int cq = warp >> 2, q4 = warp & 3;
         const int row = q4 * 32 + lane;
-        const int T = kGroups * kRows;
-        const int col = gi * kRows + row;
-        const bool owner = hf == 0;
-        double *tred = red + (size_t)gi * 2 * 4 * ns * 2;
-        double *tsum = bsum + (size_t)gi * 4 * n * ns;
-        unsigned char *xptr = sm + lay.x + gi * 2 * kTileBytes;
-        unsigned char *uptr = sm + lay.u + gi * KB0 * kTileBytes;
-        const uint32_t dcol = tmem + ((uint32_t)(q4 * 32) << 16) + gi * 2 * kH;
-        float *st = a.state + (size_t)blockIdx.x * n * T + col;
+        const bool owner = cq == 0;
+        const int m0 = 16 * cq - 1;                     // rate of this warp's first column
+        const uint32_t dq = tmem + ((uint32_t)(q4 * 32) << 16);
+        float *st = reinterpret_cast<float *>(sm + lay.state) + row; // [rate][path]: + (m - 1) T + gi * kRows
+        float *lw = reinterpret_cast<float *>(sm + lay.lc) + warp * 32; // lambda, C of rates m0 .. m0 + 15
         const float h = a.h;
-        uint32_t phd = 0, php = 0;
-        uint64_t job = 0;
+        uint32_t phd = 0, php = 0, phe = 0; // bit gi: phase parity of dnb[gi]
         int mcount = 0;
         bool ok = true;
+        // feature chunks 2 cq, 2 cq + 1 of the row at time index k: column c holds t
+        // (c = 0), u_0 = 0 (c = 1) or u_{c-1} s_u
+        auto write_features = [&](int k, int gi) {
+            const float xt = (float)k * h * g.sc.t_scale;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int c8 = 2 * cq + q;
+                if (c8 >= KB0 * 8) continue;
+                float f[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int c = c8 * 8 + e, m = c - 1;
+                    f[e] = c == 0 ? xt : ((m >= 1 && m <= n) ? st[(size_t)(m - 1) * T + gi * kRows] * g.sc.u_scale : 0.0f);
+                }
+                *reinterpret_cast<uint4 *>(sm + lay.u + gi * KB0 * kTileBytes + chunk_off(row, c8 >> 3, c8 & 7)) =
+                    make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
+            }
+        };
         for (uint64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-            const uint64_t lp = tile * (uint64_t)T + col;
-            const bool active = lp < a.paths;
-            const uint64_t p = a.first_path + lp;
-            uint64_t sidx = ~0ull;
-            if (owner && a.snap != nullptr && active && lp % a.snap_stride == 0 && lp / a.snap_stride < a.n_snap)
-                sidx = lp / a.snap_stride;
-            if (owner)
-                for (int l = 0; l < n; ++l) st[(size_t)l * T] = 0.0f;
+            const uint64_t lp0 = tile * (uint64_t)T + row; // + gi * kRows
+            if (!owner && mcount > 0) {
+                // the owners price the previous tiles' last maturity from every rate's
+                // state: wait for their payoff partials before resetting this warp's rates
+                if (!warp_wait(payb, (uint32_t)((mcount - 1) & 1), abort, g.err)) { ok = false; break; }
+            }
+            for (int m = m0 < 1 ? 1 : m0; m <= m0 + 15 && m <= n; ++m)
+#pragma unroll
+                for (int gi = 0; gi < kGroups; ++gi) st[(size_t)(m - 1) * T + gi * kRows] = 0.0f;
+            for (int gi = 0; gi < kGroups; ++gi) write_features(0, gi);
+            fence_async_smem();
+            tc_before();
+            __syncwarp();
+            if (lane == 0)
+                for (int gi = 0; gi < kGroups; ++gi) mbar_arrive(&opu[gi]);
             for (int k = 0; ok && k < S; ++k) {
                 const int imin = k / s + 1;
                 const bool mat = (k + 1) % s == 0;
-                float dH = 0.0f;
-                if (owner) {
-                    dH = draw_increment(a, p, (uint32_t)k);
-                    // feature row: column 0 t, 1 u_0 = 0, 1 + m u_m
-                    const float xt = (float)k * h * g.sc.t_scale;
-                    for (int c8 = 0; c8 < KB0 * 8; ++c8) {
-                        float f[8];
-#pragma unroll
-                        for (int e = 0; e < 8; ++e) {
-                            const int c = c8 * 8 + e, m = c - 1;
-                            f[e] = c == 0 ? xt : ((m >= 1 && m <= n) ? st[(size_t)(m - 1) * T] * g.sc.u_scale : 0.0f);
-                        }
-                        *reinterpret_cast<uint4 *>(uptr + chunk_off(row, c8 >> 3, c8 & 7)) =
-                            make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
-                    }
+                // this warp's rates at t_k: lambda, C
+                if (lane < 16) {
+                    const int m = m0 + lane;
+                    const bool in = m >= 1 && m <= n;
+                    lw[lane] = in ? a.row[(size_t)k * n + (m - 1)].x : 0.0f;
+                    lw[16 + lane] = in ? g.Ctab[(size_t)k * n + (m - 1)] : 0.0f;
                 }
-                fence_async_smem();
-                tc_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&opu[gi]);
+                float dH[kGroups];
+#pragma unroll
+                for (int gi = 0; gi < kGroups; ++gi) dH[gi] = draw_increment(a, a.first_path + lp0 + gi * kRows, (uint32_t)k);
+                // hidden layers: SiLU of 32 columns, BF16 activations into TMEM
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
-                    if (!ok) continue;
-                    if (!warp_wait(&dnb[gi], phd, abort, g.err)) { ok = false; continue; }
-                    phd ^= 1;
-                    tc_after();
-                    const uint32_t dbuf = dcol + (uint32_t)(job & 1) * kH + hf * 64;
-                    ++job;
-                    const float *hbl = bias + l * kH + hf * 64;
-                    uint32_t ra[16], rb[16];
-                    tmem_ld16(dbuf, ra);
-                    tmem_wait16(ra);
 #pragma unroll
-                    for (int cc = 0; cc < 4; ++cc) {
-                        uint32_t(&cur)[16] = (cc & 1) ? rb : ra;
-                        uint32_t(&nxt)[16] = (cc & 1) ? ra : rb;
-                        if (cc < 3) tmem_ld16(dbuf + (cc + 1) * 16, nxt);
+                    for (int gi = 0; gi < kGroups; ++gi) {
+                        if (!ok) continue;
+                        if (!warp_wait(&dnb[gi], (phd >> gi) & 1u, abort, g.err)) { ok = false; continue; }
+                        phd ^= 1u << gi;
+                        tc_after();
+                        const uint32_t dbuf = dq + gi * kH + cq * 32;
+                        const float *hbl = bias + l * kH + cq * 32;
+                        uint32_t ra[16], rb[16];
+                        tmem_ld16(dbuf, ra);
+                        tmem_wait16(ra);
+                        tmem_ld16(dbuf + 16, rb);
 #pragma unroll
-                        for (int qd = 0; qd < 2; ++qd) {
-                            float sv[8];
-                            silu8(cur + qd * 8, hbl + cc * 16 + qd * 8, sv);
-                            *reinterpret_cast<uint4 *>(xptr + chunk_off(row, hf, cc * 2 + qd)) =
-                                make_uint4(pack2(sv[0], sv[1]), pack2(sv[2], sv[3]), pack2(sv[4], sv[5]),
-                                           pack2(sv[6], sv[7]));
+                        for (int cc = 0; cc < 2; ++cc) {
+                            uint32_t(&cur)[16] = cc ? rb : ra;
+                            uint32_t pk[8];
+#pragma unroll
+                            for (int qd = 0; qd < 2; ++qd) {
+                                float sv[8];
+                                silu8(cur + qd * 8, hbl + cc * 16 + qd * 8, sv);
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) pk[qd * 4 + e] = pack2(sv[2 * e], sv[2 * e + 1]);
+                            }
+                            tmem_st8(dq + 2 * kH + gi * (kH / 2) + cq * 16 + cc * 8, pk);
+                            if (cc == 0) tmem_wait16(rb);
                         }
-                        if (cc < 3) tmem_wait16(nxt);
+                        tmem_wait_st();
+                        tc_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&opx[gi]);
                     }
+                }
+                // output product: this warp's 16 rates, Euler step and next feature columns
+#pragma unroll
+                for (int gi = 0; gi < kGroups; ++gi) {
+                    if (!ok) continue;
+                    if (!warp_wait(&dnb[gi], (phd >> gi) & 1u, abort, g.err)) { ok = false; continue; }
+                    phd ^= 1u << gi;
+                    tc_after();
+                    uint32_t ro[16];
+                    tmem_ld16(dq + gi * kH + cq * 16, ro);
+                    tmem_wait16(ro);
+                    const uint64_t lp = lp0 + gi * kRows;
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const int m = m0 + c;
+                        if (m < imin || m > n) continue; // also m < 1: imin >= 1
+                        const float f = __uint_as_float(ro[c]) + bout[16 * cq + c];
+                        const float A = lw[16 + c] + g.sc.y_scale * f;
+                        float *sp = st + (size_t)(m - 1) * T + gi * kRows;
+                        const float z = sp[0] + fmaf(lw[c], dH[gi], -A * h);
+                        sp[0] = z;
+                        if (mat && a.snap != nullptr && lp < a.paths && lp % a.snap_stride == 0 &&
+                            lp / a.snap_stride < a.n_snap)
+                            a.snap[((size_t)(imin - 1) * n + (m - 1)) * a.snap_pitch + lp / a.snap_stride] = z + a.Z0[m - 1];
+                    }
+                }
+                if (!ok) break;
+                // next step's feature columns of these rates; accumulators read
+                if (k + 1 < S) {
+                    for (int gi = 0; gi < kGroups; ++gi) write_features(k + 1, gi);
                     fence_async_smem();
                     tc_before();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&opx[gi]);
-                }
-                // output product: every rate's f, read by the row's owner
-                if (ok && !warp_wait(&dnb[gi], phd, abort, g.err)) ok = false;
-                if (!ok) break;
-                phd ^= 1;
-                tc_after();
-                const uint32_t obuf = dcol + (uint32_t)(job & 1) * kH;
-                ++job;
-                if (owner) {
-                    uint32_t r0[16], r1[16], r2[16];
-                    tmem_ld16(obuf, r0);
-                    tmem_ld16(obuf + 16, r1);
-                    tmem_ld16(obuf + 32, r2);
-                    tmem_wait16(r0);
-                    tmem_wait16(r1);
-                    tmem_wait16(r2);
-                    float fo[kOut];
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) {
-                        fo[c] = __uint_as_float(r0[c]) + bout[c];
-                        fo[16 + c] = __uint_as_float(r1[c]) + bout[16 + c];
-                        fo[32 + c] = __uint_as_float(r2[c]) + bout[32 + c];
-                    }
-                    tc_before();
-                    // Euler step of every live rate with A_i = C_i + s_y f_{i-1}
-#pragma unroll
-                    for (int i = kOut; i >= 1; --i) {
-                        if (i > n || i < imin) continue;
-                        const size_t rowk = (size_t)k * n + (i - 1);
-                        float *sp = st + (size_t)(i - 1) * T;
-                        const float A = g.Ctab[rowk] + g.sc.y_scale * fo[i - 1];
-                        const float z = sp[0] + fmaf(a.row[rowk].x, dH, -A * h);
-                        sp[0] = z;
-                        if (mat && sidx != ~0ull)
-                            a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = z + a.Z0[i - 1];
-                    }
+                    if (lane == 0)
+                        for (int gi = 0; gi < kGroups; ++gi) mbar_arrive(&opu[gi]);
                 } else {
                     tc_before();
                 }
-                if (mat && owner) {
+                if (mat) {
+                    // the owner warps price with every rate of the row's paths
+                    if (!owner) {
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(eul);
+                        ++mcount; // the owners' payoff phases, counted alike
+                        continue;
+                    }
+                    if (!warp_wait(eul, phe, abort, g.err)) { ok = false; break; }
+                    phe ^= 1;
                     const int m = imin, buf = mcount & 1;
                     ++mcount;
-                    double Pp, Sp;
-                    float Lm;
-                    maturity_products(a, m, [&](int i) { return st[(size_t)(i - 1) * T] + a.Z0[i - 1]; }, Pp, Sp, Lm);
+                    double Pp[kGroups], Sp[kGroups];
+                    float Lm[kGroups];
+#pragma unroll
+                    for (int gi = 0; gi < kGroups; ++gi)
+                        maturity_products(a, m, [&](int i) { return st[(size_t)(i - 1) * T + gi * kRows] + a.Z0[i - 1]; },
+                                          Pp[gi], Sp[gi], Lm[gi]);
                     for (int qs = 0; qs < ns; ++qs) {
                         const float K = a.strikes[(size_t)(m - 1) * ns + qs];
-                        const double pay = active ? payoff(a, Pp, Sp, Lm, K) : 0.0;
-                        const double s1 = warp_sum(pay);
-                        const double s2 = warp_sum(pay * pay);
+                        double s1 = 0.0, s2 = 0.0;
+#pragma unroll
+                        for (int gi = 0; gi < kGroups; ++gi) {
+                            const double pay = lp0 + gi * kRows < a.paths ? payoff(a, Pp[gi], Sp[gi], Lm[gi], K) : 0.0;
+                            s1 += pay;
+                            s2 += pay * pay;
+                        }
+                        s1 = warp_sum(s1);
+                        s2 = warp_sum(s2);
                         if (lane == 0) {
-                            tred[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 0] = s1;
-                            tred[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 1] = s2;
+                            red[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 0] = s1;
+                            red[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 1] = s2;
                         }
                     }
-                    if (lane == 0) mbar_arrive(&payb[gi]);
+                    if (lane == 0) mbar_arrive(payb);
                     if (q4 == 0) {
-                        if (!warp_wait(&payb[gi], php, abort, g.err)) { ok = false; break; }
+                        if (!warp_wait(payb, php, abort, g.err)) { ok = false; break; }
                         if (lane == 0) {
                             for (int qs = 0; qs < ns; ++qs) {
                                 double s1 = 0.0, s2 = 0.0;
                                 for (int wv = 0; wv < 4; ++wv) {
-                                    s1 += tred[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 0];
-                                    s2 += tred[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 1];
+                                    s1 += red[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 0];
+                                    s2 += red[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 1];
                                 }
-                                double *acc = tsum + 4 * ((size_t)(m - 1) * ns + qs);
+                                double *acc = bsum + 4 * ((size_t)(m - 1) * ns + qs);
                                 kahan_add(acc + 0, acc + 1, s1);
                                 kahan_add(acc + 2, acc + 3, s2);
                             }
@@ -958,12 +1008,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
     __syncthreads();
     if (warp == kEpiWarps) {
         tc_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kGroups * 2 * kH));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * kH));
     }
     double *out = a.partials + (size_t)blockIdx.x * n * ns * 2;
     for (int e = tid; e < n * ns; e += kThreads) {
-        out[2 * e + 0] = bsum[4 * e + 0] + bsum[4 * ((size_t)n * ns + e) + 0];
-        out[2 * e + 1] = bsum[4 * e + 2] + bsum[4 * ((size_t)n * ns + e) + 2];
+        out[2 * e + 0] = bsum[4 * e + 0];
+        out[2 * e + 1] = bsum[4 * e + 2];
     }
 }
 
