@@ -678,7 +678,7 @@ constexpr int kOutN = 64;                      // output product width: columns 
 constexpr int kOutBlock = kOutN * 128;         // one 64-wide K block of the staged W_out
 
 struct TcVecLayout {
-    uint32_t w0, w, wo, u, bias, bout, bars, misc, red, bsum, state, lc, total;
+    uint32_t w0, w, wo, u, bias, bout, bars, misc, red, bsum, state, lc, dh, total;
 };
 
 __host__ __device__ inline TcVecLayout tc_vec_layout(int L, int KB0, int n, int ns)
@@ -698,6 +698,7 @@ __host__ __device__ inline TcVecLayout tc_vec_layout(int L, int KB0, int n, int 
     t.bsum = o; o += n * ns * 4 * 8;              // Kahan accumulators
     t.state = o; o += n * kGroups * kRows * 4;    // log-rate offsets of the CTA's paths, [rate][path]
     t.lc = o; o += kEpiWarps * 2 * 16 * 4;        // per warp: lambda and C of its 16 rates at t_k
+    t.dh = o; o += 2 * kGroups * kRows * 4;       // increments of the CTA's paths, two steps
     t.total = o + 1024;                           // slack for aligning the base
     return t;
 }
@@ -720,6 +721,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
     uint64_t *eul = bars + 6;   // Euler steps of quarters 1..3 done, at a maturity (12 warps)
     uint64_t *payb = bars + 7;  // payoff partials written (the 4 path-owning warps)
     uint64_t *finb = bars + 8;  // all products complete (commit)
+    uint64_t *dhb = bars + 9;   // [2] a step's increments written (quarters 0 and 1, one tile each), by step parity
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + lay.misc);
     volatile int *abort = reinterpret_cast<volatile int *>(sm + lay.misc + 4);
     double *red = reinterpret_cast<double *>(sm + lay.red);
@@ -756,6 +758,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
         mbar_init(eul, 12);
         mbar_init(payb, 4);
         mbar_init(finb, 1);
+        mbar_init(&dhb[0], 4 * kGroups);
+        mbar_init(&dhb[1], 4 * kGroups);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -826,8 +830,10 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
         float *st = reinterpret_cast<float *>(sm + lay.state) + row; // [rate][path]: + (m - 1) T + gi * kRows
         float *lw = reinterpret_cast<float *>(sm + lay.lc) + warp * 32; // lambda, C of rates m0 .. m0 + 15
         const float h = a.h;
-        uint32_t phd = 0, php = 0, phe = 0; // bit gi: phase parity of dnb[gi]
+        uint32_t phd = 0, php = 0, phe = 0, phh = 0; // bit gi: phase parity of dnb[gi]; bit b: of dhb[b]
         int mcount = 0;
+        uint64_t gstep = 0; // steps begun by this CTA: a step's increments live in buffer gstep & 1
+        float *dhs = reinterpret_cast<float *>(sm + lay.dh) + row; // [buffer][tile][row]
         bool ok = true;
         // feature chunks 2 cq, 2 cq + 1 of the row at time index k: column c holds t
         // (c = 0), u_0 = 0 (c = 1) or u_{c-1} s_u
@@ -863,9 +869,20 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
             __syncwarp();
             if (lane == 0)
                 for (int gi = 0; gi < kGroups; ++gi) mbar_arrive(&opu[gi]);
+            // each step's increments are drawn once, tile gi by the warps of column
+            // quarter gi, and shared with the others (two buffers and barriers,
+            // alternating by step)
+            auto draw_share = [&](int kk, int b) {
+                dhs[(b * kGroups + cq) * kRows] = draw_increment(a, a.first_path + lp0 + cq * kRows, (uint32_t)kk);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&dhb[b]);
+            };
+            const bool drawer = cq < kGroups;
+            if (drawer) draw_share(0, (int)(gstep & 1));
             for (int k = 0; ok && k < S; ++k) {
                 const int imin = k / s + 1;
                 const bool mat = (k + 1) % s == 0;
+                const int gb = (int)(gstep++ & 1);
                 // this warp's rates at t_k: lambda, C
                 if (lane < 16) {
                     const int m = m0 + lane;
@@ -874,9 +891,6 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
                     lw[16 + lane] = in ? g.Ctab[(size_t)k * n + (m - 1)] : 0.0f;
                 }
                 __syncwarp();
-                float dH[kGroups];
-#pragma unroll
-                for (int gi = 0; gi < kGroups; ++gi) dH[gi] = draw_increment(a, a.first_path + lp0 + gi * kRows, (uint32_t)k);
                 // hidden layers: SiLU of 32 columns, BF16 activations into TMEM
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
@@ -913,6 +927,13 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
                     }
                 }
                 // output product: this warp's 16 rates, Euler step and next feature columns
+                if (ok) {
+                    if (!warp_wait(&dhb[gb], (phh >> gb) & 1u, abort, g.err)) ok = false;
+                    phh ^= 1u << gb;
+                }
+                float dH[kGroups];
+#pragma unroll
+                for (int gi = 0; gi < kGroups; ++gi) dH[gi] = dhs[(gb * kGroups + gi) * kRows];
 #pragma unroll
                 for (int gi = 0; gi < kGroups; ++gi) {
                     if (!ok) continue;
@@ -946,6 +967,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
                     __syncwarp();
                     if (lane == 0)
                         for (int gi = 0; gi < kGroups; ++gi) mbar_arrive(&opu[gi]);
+                    if (drawer) draw_share(k + 1, (int)(gstep & 1));
                 } else {
                     tc_before();
                 }
