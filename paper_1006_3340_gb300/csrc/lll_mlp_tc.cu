@@ -218,6 +218,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&r)[16])
                  : "r"(ta));
 }
 
+// 8 consecutive columns into r[0..7] (completed by tmem_wait16 on the enclosing array)
+__device__ __forceinline__ void tmem_ld8(uint32_t ta, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(ta));
+}
+
 __device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16])
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;" : LLL_R16(r) : : "memory");
@@ -669,9 +677,9 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
 // paths, sixteen epilogue warps shared by both tiles, activations in TMEM, one
 // MMA lane).  W_out's rows are staged two columns down, so that output column c
 // belongs to rate c - 1, the rate whose log-rate sits in feature column c: the
-// warp of column quarter cq reads its 16 output columns, applies the Euler
-// step of those rates and writes their feature columns for the next step,
-// with no exchange between warps.
+// warp of column quarter cq reads its 16 output columns (chunks cq and cq + 4),
+// applies the Euler step of those rates and writes their feature columns for
+// the next step, with no exchange between warps.
 // ---------------------------------------------------------------------------
 constexpr int kOut = 48;                       // network outputs (column i - 1 for rate i; n <= 48)
 constexpr int kOutN = 64;                      // output product width: columns 0 .. 63, rate c - 1
@@ -721,7 +729,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
     uint64_t *eul = bars + 6;   // Euler steps of quarters 1..3 done, at a maturity (12 warps)
     uint64_t *payb = bars + 7;  // payoff partials written (the 4 path-owning warps)
     uint64_t *finb = bars + 8;  // all products complete (commit)
-    uint64_t *dhb = bars + 9;   // [2] a step's increments written (quarters 0 and 1, one tile each), by step parity
+    uint64_t *dhb = bars + 9;   // [2] a step's increments written (quarters 2 and 3, one tile each), by step parity
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + lay.misc);
     volatile int *abort = reinterpret_cast<volatile int *>(sm + lay.misc + 4);
     double *red = reinterpret_cast<double *>(sm + lay.red);
@@ -820,15 +828,17 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
         __syncwarp();
     } else {
         // warp = 4 cq + q4: TMEM lane quadrant q4 (row 32 q4 + lane of each tile) and
-        // column quarter cq: columns 32 cq .. +31 of the hidden layers, output and
-        // feature columns 16 cq .. +15, that is rates 16 cq - 1 .. 16 cq + 14.
+        // column quarter cq: columns 32 cq .. +31 of the hidden layers; output and
+        // feature columns 8 cq .. +7 and 8 cq + 32 .. +39 (chunks cq and cq + 4, so
+        // that the live rates spread evenly), that is rates column - 1.
         const int cq = warp >> 2, q4 = warp & 3;
         const int row = q4 * 32 + lane;
         const bool owner = cq == 0;
-        const int m0 = 16 * cq - 1;                     // rate of this warp's first column
+        // output / feature column of this warp's c-th rate (c = 0 .. 15)
+        auto col_of = [&](int c) { return (c < 8 ? 8 * cq : 8 * cq + 24) + c; };
         const uint32_t dq = tmem + ((uint32_t)(q4 * 32) << 16);
         float *st = reinterpret_cast<float *>(sm + lay.state) + row; // [rate][path]: + (m - 1) T + gi * kRows
-        float *lw = reinterpret_cast<float *>(sm + lay.lc) + warp * 32; // lambda, C of rates m0 .. m0 + 15
+        float *lw = reinterpret_cast<float *>(sm + lay.lc) + warp * 32; // lambda, C of this warp's 16 rates
         const float h = a.h;
         uint32_t phd = 0, php = 0, phe = 0, phh = 0; // bit gi: phase parity of dnb[gi]; bit b: of dhb[b]
         int mcount = 0;
@@ -841,7 +851,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
             const float xt = (float)k * h * g.sc.t_scale;
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-                const int c8 = 2 * cq + q;
+                const int c8 = cq + 4 * q;
                 if (c8 >= KB0 * 8) continue;
                 float f[8];
 #pragma unroll
@@ -860,9 +870,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
                 // state: wait for their payoff partials before resetting this warp's rates
                 if (!warp_wait(payb, (uint32_t)((mcount - 1) & 1), abort, g.err)) { ok = false; break; }
             }
-            for (int m = m0 < 1 ? 1 : m0; m <= m0 + 15 && m <= n; ++m)
+            for (int c = 0; c < 16; ++c) {
+                const int m = col_of(c) - 1;
+                if (m >= 1 && m <= n)
 #pragma unroll
-                for (int gi = 0; gi < kGroups; ++gi) st[(size_t)(m - 1) * T + gi * kRows] = 0.0f;
+                    for (int gi = 0; gi < kGroups; ++gi) st[(size_t)(m - 1) * T + gi * kRows] = 0.0f;
+            }
             for (int gi = 0; gi < kGroups; ++gi) write_features(0, gi);
             fence_async_smem();
             tc_before();
@@ -870,14 +883,15 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
             if (lane == 0)
                 for (int gi = 0; gi < kGroups; ++gi) mbar_arrive(&opu[gi]);
             // each step's increments are drawn once, tile gi by the warps of column
-            // quarter gi, and shared with the others (two buffers and barriers,
+            // quarter 2 + gi, and shared with the others (two buffers and barriers,
             // alternating by step)
             auto draw_share = [&](int kk, int b) {
-                dhs[(b * kGroups + cq) * kRows] = draw_increment(a, a.first_path + lp0 + cq * kRows, (uint32_t)kk);
+                const int gi = cq - (4 - kGroups);
+                dhs[(b * kGroups + gi) * kRows] = draw_increment(a, a.first_path + lp0 + gi * kRows, (uint32_t)kk);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&dhb[b]);
             };
-            const bool drawer = cq < kGroups;
+            const bool drawer = cq >= 4 - kGroups; // quarters 2 and 3: the fewest low-index rates
             if (drawer) draw_share(0, (int)(gstep & 1));
             for (int k = 0; ok && k < S; ++k) {
                 const int imin = k / s + 1;
@@ -885,7 +899,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
                 const int gb = (int)(gstep++ & 1);
                 // this warp's rates at t_k: lambda, C
                 if (lane < 16) {
-                    const int m = m0 + lane;
+                    const int m = col_of(lane) - 1;
                     const bool in = m >= 1 && m <= n;
                     lw[lane] = in ? a.row[(size_t)k * n + (m - 1)].x : 0.0f;
                     lw[16 + lane] = in ? g.Ctab[(size_t)k * n + (m - 1)] : 0.0f;
@@ -941,14 +955,15 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
                     phd ^= 1u << gi;
                     tc_after();
                     uint32_t ro[16];
-                    tmem_ld16(dq + gi * kH + cq * 16, ro);
+                    tmem_ld8(dq + gi * kH + 8 * cq, ro);
+                    tmem_ld8(dq + gi * kH + 8 * cq + 32, ro + 8);
                     tmem_wait16(ro);
                     const uint64_t lp = lp0 + gi * kRows;
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {
-                        const int m = m0 + c;
+                        const int m = col_of(c) - 1;
                         if (m < imin || m > n) continue; // also m < 1: imin >= 1
-                        const float f = __uint_as_float(ro[c]) + bout[16 * cq + c];
+                        const float f = __uint_as_float(ro[c]) + bout[col_of(c)];
                         const float A = lw[16 + c] + g.sc.y_scale * f;
                         float *sp = st + (size_t)(m - 1) * T + gi * kRows;
                         const float z = sp[0] + fmaf(lw[c], dH[gi], -A * h);
