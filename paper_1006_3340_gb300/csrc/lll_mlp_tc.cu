@@ -893,18 +893,23 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
             };
             const bool drawer = cq >= 4 - kGroups; // quarters 2 and 3: the fewest low-index rates
             if (drawer) draw_share(0, (int)(gstep & 1));
+            // this warp's rates' lambda and C, loaded one step ahead of their use
+            const int mine = lane < 16 ? col_of(lane) - 1 : 0;
+            const bool in = lane < 16 && mine >= 1 && mine <= n;
+            float lam_next = in ? a.row[mine - 1].x : 0.0f, c_next = in ? g.Ctab[mine - 1] : 0.0f;
             for (int k = 0; ok && k < S; ++k) {
                 const int imin = k / s + 1;
                 const bool mat = (k + 1) % s == 0;
                 const int gb = (int)(gstep++ & 1);
-                // this warp's rates at t_k: lambda, C
                 if (lane < 16) {
-                    const int m = col_of(lane) - 1;
-                    const bool in = m >= 1 && m <= n;
-                    lw[lane] = in ? a.row[(size_t)k * n + (m - 1)].x : 0.0f;
-                    lw[16 + lane] = in ? g.Ctab[(size_t)k * n + (m - 1)] : 0.0f;
+                    lw[lane] = lam_next;
+                    lw[16 + lane] = c_next;
                 }
                 __syncwarp();
+                if (in && k + 1 < S) {
+                    lam_next = a.row[(size_t)(k + 1) * n + (mine - 1)].x;
+                    c_next = g.Ctab[(size_t)(k + 1) * n + (mine - 1)];
+                }
                 // hidden layers: SiLU of 32 columns, BF16 activations into TMEM
 #pragma unroll
                 for (int l = 0; l < L; ++l) {
