@@ -8,26 +8,29 @@
 // and f the trained network (SiLU hidden layers, BF16 weights and
 // activations, FP32 accumulation).
 //
-// Roles of a CTA (544 threads):
-//  * warps 0-15: epilogue.  Warps 8g .. 8g+7 serve path tile g (128 paths,
-//    one per TMEM lane): warp 8g + 4hf + q reads lane quadrant q, columns
-//    64hf .. 64hf+63 of the tile's accumulator, so two threads share a row.
-//    They turn each layer's accumulator into the next layer's BF16 operand
-//    (bias + SiLU) and evaluate their half of the output layer; the hf = 0
-//    thread of a row owns the path: it draws the increments, writes the
-//    feature row, adds the other half's output partial, and makes the Euler
-//    step and the caplet bookkeeping.
-//  * warp 16: allocates 512 TMEM columns (two 128-column accumulators per
-//    tile, used alternately so that the next rate's first layer overlaps the
-//    current rate's last epilogue) and, from one lane, issues the MMAs.  Every layer of every
-//    live rate is one 128 x H x K product D = X W^T (kind::f16, BF16 operands
-//    K-major with 128-byte swizzle in shared memory, FP32 D in TMEM), the
-//    tiles taking turns so that one's epilogue overlaps the other's MMA.
+// Roles of a CTA (544 threads), per-rate network (mlp_tc_kernel):
+//  * warp 16: allocates 512 TMEM columns and, from one lane, issues the
+//    products of both path tiles in turn (128 paths each, one per TMEM lane).
+//    Per live rate and tile: the first layer from the feature rows in shared
+//    memory (128-byte swizzled, K-major), then the hidden layers with the
+//    previous layer's BF16 activations as the A operand in TMEM; every product
+//    accumulates FP32 into the tile's 128-column accumulator.  t, i and
+//    lambda_i are the same for every path of a (step, rate), so they enter the
+//    first layer as a per-rate bias and the feature rows change once per step.
+//  * warps 0-15: epilogue, warp 4 cq + q: TMEM lane quadrant q and column
+//    quarter cq.  Every warp works on both tiles, one layer at a time in turn:
+//    it reads 32 accumulator columns, adds the bias, applies SiLU and writes
+//    the next layer's activations with tcgen05.st, or forms its quarter of the
+//    output dot product.  The cq = 0 thread of a row owns the row's path in
+//    both tiles: increments, feature rows, the Euler step (one rate late, off
+//    the products' critical path) and the caplet bookkeeping.  Path state and
+//    the step's lambda and C rows are kept in shared memory.
 // Weights stay in shared memory for the whole launch.  Hand-offs use
-// mbarriers: "operand ready" (one arrival per warp of the tile, after every
-// lane's proxy fence), "accumulator ready" (tcgen05.commit) and "output
-// partial ready".  Every wait is bounded: on timeout the CTA sets an
-// error word, abandons its work and releases its tensor memory.
+// mbarriers (operand ready: one arrival per epilogue warp; accumulator ready:
+// tcgen05.commit; output partials ready).  Every wait first tests the phase
+// and then waits boundedly: on timeout the CTA sets an error word, abandons
+// its work and releases its tensor memory.  The vector-head kernel
+// (mlp_tc_vec_kernel) below shares this layout.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -308,15 +311,16 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
     float *wout = reinterpret_cast<float *>(sm + lay.wout);
     float *w0c = reinterpret_cast<float *>(sm + lay.w0c);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + lay.bars);
-    // Operand-ready barriers, one arrival per warp of the tile: feature rows
-    // (first layer) and activations (hidden layers) have separate barriers, so
-    // a warp never arrives twice on one barrier before its phase completed
-    // (every arrival on either is preceded by a wait for the previous product).
-    uint64_t *opu = bars + 0;  // [kGroups] feature row ready
+    // Operand-ready barriers, one arrival per epilogue warp: feature rows and a
+    // free accumulator (first layer) and activations (hidden layers) have
+    // separate barriers, so a warp never arrives twice on one barrier before
+    // its phase completed (every arrival on either is preceded by a wait for
+    // the previous product).
+    uint64_t *opu = bars + 0;  // [kGroups] feature rows written, accumulator free
     uint64_t *opx = bars + 2;  // [kGroups] activations ready
     uint64_t *dnb = bars + 4;  // [kGroups] accumulator ready (commit)
-    uint64_t *outb = bars + 6; // [kGroups] upper-half output partials written (4 arrivals)
-    uint64_t *payb = bars + 8; // [kGroups] payoff partials of a tile written (its 4 owner warps)
+    uint64_t *outb = bars + 6; // [kGroups] output partials of column quarters 1..3 written (12 arrivals)
+    uint64_t *payb = bars + 8; // payoff partials written (the 4 path-owning warps; payb[0] only)
     uint64_t *finb = bars + 10; // all MMAs complete (commit)
     uint32_t *tslot = reinterpret_cast<uint32_t *>(sm + lay.misc);
     volatile int *abort = reinterpret_cast<volatile int *>(sm + lay.misc + 4);
