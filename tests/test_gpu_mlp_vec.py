@@ -156,3 +156,28 @@ def test_tcgen05_and_layered_vector_head_agree(lll, trained_vec):
     assert np.abs(z_t[mask] - z_l[mask]).max() <= 2e-6
     assert np.abs(p_t - p_l).max() <= 1e-9
     assert np.abs(p_tr - p_lr).max() <= 1e-9
+
+
+def test_vector_head_bounded_waits_give_up_and_context_stays_usable(lll, trained_vec):
+    """Failure detection of the vector-head kernel without a GPU fault: with
+    LLL_INJECT_MMA_STALL its MMA lane issues nothing, so every bounded wait
+    runs out. Those are the product waits and the increment and maturity
+    barriers between column quarters. The launch ends by itself, the results
+    read back as LLL_ETIMEOUT (-4), and the next simulation on the same context
+    reproduces the reference prices bit for bit."""
+    wl, x, W, sim, loss = trained_vec
+    cnt = 4096
+    try:
+        lll.lll_mlp_set_kernel(sim.ctx, "tc")
+        sim.simulate("mlp", paths=cnt)
+        ref, _ = sim.prices()
+        lll.lll_inject(sim.ctx, lll.LLL_INJECT_MMA_STALL)
+        sim.simulate("mlp", paths=cnt)
+        with pytest.raises(lll.LLLError) as e:
+            sim.prices()
+        assert e.value.code == -4
+        sim.simulate("mlp", paths=cnt)
+        again, _ = sim.prices()
+    finally:
+        lll.lll_mlp_set_kernel(sim.ctx, "auto")
+    assert np.array_equal(ref, again)
