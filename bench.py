@@ -137,10 +137,12 @@ def _peaks():
         return {}
 
 
-def cpu_baseline(wl, schemes, budget_s=12.0, threads=None):
+def cpu_baseline(wl, schemes, budget_s=12.0, threads=None, mlp=None):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
     batches of paths (the same global paths the GPU simulates first)
-    alternating schemes until the time budget is used."""
+    alternating the quadrature schemes until the time budget is used, then a
+    single-thread figure on a small batch, and (``mlp`` = (params, scales,
+    head)) the FP64 oracle of the learned-compensator scheme on a few paths."""
     from oracle import oracle as ora
     from oracle import quadrature
 
@@ -149,77 +151,114 @@ def cpu_baseline(wl, schemes, budget_s=12.0, threads=None):
     threads = threads or os.cpu_count() or 1
     codes = {"picard": ora.PICARD, "full": ora.FULL, "frozen": ora.FROZEN}
     batch = 1024 if wl.N <= 61 else 128  # the N=120 oracle costs about 30x more per path
-    units = 0
-    done = {s: 0 for s in schemes}
+    done = {s: 0 for s in schemes if s in codes}
+    secs = {s: 0.0 for s in done}
     t0 = time.perf_counter()
-    while True:
-        for s in schemes:
-            if s not in codes:
-                continue
+    while done:
+        for s in done:
+            t1 = time.perf_counter()
             ora.simulate(model, codes[s], path0=done[s], npaths=batch, threads=threads)
+            secs[s] += time.perf_counter() - t1
             done[s] += batch
-            units += batch * wl.units_per_path()
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    sample = ", ".join(f"{s}: paths 0..{done[s] - 1}" for s in done if s in codes)
-    return {"value": units / dt, "unit": "path·tenor·steps/s", "cores": threads, "kind": "oracle",
-            "sample": f"{wl.name} ({sample}); FP64 C oracle, {threads} threads, {dt:.1f} s"}
+    units = sum(done.values()) * wl.units_per_path()
+    per = {s: done[s] * wl.units_per_path() / secs[s] for s in done}
+    sample = ", ".join(f"{s}: paths 0..{done[s] - 1}" for s in done)
+    out = {"value": units / dt, "unit": "path·tenor·steps/s", "cores": threads, "kind": "oracle",
+           "sample": f"{wl.name} ({sample}); FP64 C oracle, {threads} threads, {dt:.1f} s",
+           "per_scheme": per}
+    # one thread, the first quadrature scheme, a small batch
+    if done:
+        s1 = next(iter(done))
+        p1 = 64 if wl.N <= 61 else 8
+        t1 = time.perf_counter()
+        ora.simulate(model, codes[s1], path0=0, npaths=p1, threads=1)
+        out["value_1_thread"] = p1 * wl.units_per_path() / (time.perf_counter() - t1)
+        out["sample_1_thread"] = f"{s1}, paths 0..{p1 - 1}, 1 thread"
+    if mlp is not None:
+        from oracle import mlp as omlp
+        params, scales, head = mlp
+        pm = 64 if wl.N <= 61 else 4
+        t1 = time.perf_counter()
+        omlp.simulate_scheme(model, params, scales, npaths=pm, head=head)
+        out["mlp_fp64"] = {"value": pm * wl.units_per_path() / (time.perf_counter() - t1),
+                           "unit": "path·tenor·steps/s",
+                           "sample": f"learned-compensator scheme (oracle/mlp.py, numpy FP64 matrix products "
+                                     f"on the host's BLAS threads), paths 0..{pm - 1}"}
+    return out
 
 
 def run_reference(args):
     """The oracle as the reference arm: each step simulates a bounded sample of
-    the workload per scheme on the host cores."""
+    the workload per scheme on the host cores -- Picard and full with the C
+    oracle, and (where the GPU arm runs it) the learned-compensator scheme with
+    the FP64 network oracle on a seeded network of the benchmark's shape (its
+    cost does not depend on the weights)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    from oracle import mlp as omlp
     from oracle import oracle as ora
     from oracle import quadrature
 
     wl = _workload(args)
-    schemes = ["picard", "full"]
+    schemes = _schemes(args)
     x, W = quadrature.rule_for(wl)
     model = ora.OracleModel(wl, x, W)
     threads = os.cpu_count() or 1
     codes = {"picard": ora.PICARD, "full": ora.FULL}
     per_step = args.ref_paths
+    mlp_paths = max(per_step // 16, 8)
+    hid, lay = _arch(wl)
+    params = omlp.init_params([wl.N + 3] + [hid] * lay + [1], seed=3)
+    scales = np.array([1.0 / (wl.n * wl.delta), 1.0 / wl.n, 5.0, 4.0, 1e-4])
+
+    def step(k, scale=1):
+        units = 0
+        for s in schemes:
+            if s in codes:
+                npaths = max(per_step // scale, threads)
+                ora.simulate(model, codes[s], path0=k * per_step, npaths=npaths, threads=threads)
+            elif s == "mlp":
+                npaths = max(mlp_paths // scale, 2)
+                omlp.simulate_scheme(model, params, scales, path0=k * mlp_paths, npaths=npaths)
+            else:
+                continue
+            units += npaths * wl.units_per_path()
+        return units
+
     for w in range(args.warmup):
-        for s in schemes:
-            ora.simulate(model, codes[s], path0=0, npaths=max(per_step // 8, threads), threads=threads)
+        step(0, scale=8)
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        for s in schemes:
-            ora.simulate(model, codes[s], path0=k * per_step, npaths=per_step, threads=threads)
+    units = sum(step(k) for k in range(args.steps))
     dt = time.perf_counter() - t0
-    units = args.steps * len(schemes) * per_step * wl.units_per_path()
     val = units / dt
     unit = "path·tenor·steps/s"
     line = {"metric": METRIC, "value": val, "unit": unit, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": _describe(wl, schemes), "reference_sample_paths_per_scheme": per_step},
+            "config": {"workload": _describe(wl, schemes), "reference_sample_paths_per_scheme": per_step,
+                       "reference_sample_paths_mlp": mlp_paths},
             "cpu_baseline": {"value": val, "unit": unit, "cores": threads, "kind": "oracle",
-                             "sample": f"{per_step} paths per scheme per step of {wl.name}"},
+                             "sample": f"per step {per_step} paths per quadrature scheme (C oracle) and "
+                                       f"{mlp_paths} paths of the learned scheme (numpy FP64) of {wl.name}"},
             "e2e": {"value": val, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_batch(args):
+def run_batch(args, steps, warmup, with_cpu=True, with_e2e=True, rates=None):
     """The batched configuration: 256 independent term structures of uneven tenor
     count, strike grid and path budget (2^24 paths in total) in one persistent
     launch per scheme, replayed as a CUDA graph.  One step = the Picard and the
-    full scheme over every instance.  Single GPU."""
+    full scheme over every instance.  Single GPU.  Returns the JSON line."""
     import torch
 
-    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
-        print(json.dumps({"error": "--workload batch256 runs on one GPU"}), flush=True)
-        return 1
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    from paper_1006_3340_gb300 import build as libbuild
-    libbuild.build()
     from paper_1006_3340_gb300 import autotune, lll
 
     wls = workloads.batched_instances()
@@ -244,7 +283,7 @@ def run_batch(args):
             if evs is not None:
                 evs[i][1].record()
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         one_step()
     torch.cuda.synchronize()
     sampler = ClockSampler(0)
@@ -253,7 +292,7 @@ def run_batch(args):
     per_ms = {s: [] for s in schemes}
     kernel_ms = {s: [] for s in schemes}
     torch.cuda.synchronize()
-    for k in range(args.steps):
+    for k in range(steps):
         flush.fill_(k & 0xFF)  # L2 flush between timed steps (outside the events)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in schemes]
         for i, s in enumerate(schemes):
@@ -267,32 +306,29 @@ def run_batch(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     total_ms = sum(sum(v) for v in per_ms.values())
-    value = units * len(schemes) * args.steps / (total_ms * 1e-3)
+    value = units * len(schemes) * steps / (total_ms * 1e-3)
     per = {}
     for s in schemes:
         ms = statistics.mean(per_ms[s])
         p0, _ = lll.lll_batch_prices(b, 0, wls[0].n, wls[0].strikes.shape[1])
         per[s] = {"units_per_s": units / (ms * 1e-3), "ms": ms, "batch_kernel_ms": statistics.mean(kernel_ms[s]),
                   "caplets_per_s": caplets / (ms * 1e-3), "inst0_atm_first_maturity": float(p0[0, 5])}
-    peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = sms * 128 * sm_max * 1e6 / 1e12
+    pk = _alu_peaks(lll, torch, dev, rates)
     dom = max(schemes, key=lambda s: statistics.mean(kernel_ms[s]))
     ach = lane_ops / (statistics.mean(kernel_ms[dom]) * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFP32-lane-op/s",
-                "frac": ach / fp32_peak, "traffic": None,
+    roofline = {"bound": "alu", "achieved": ach, "peak": pk["fp32"], "unit": "TFP32-lane-op/s",
+                "frac": ach / pk["fp32"], "frac_of_nominal_128_lanes": ach / pk["fp32_nominal"], "traffic": None,
                 "kernel": f"batch_kernel ({dom}), 3Q FP32 lane-ops per unit, Q=64",
-                "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS)"}
+                "peak_basis": pk["fp32_basis"]}
 
     # end to end through the C ABI from host arrays: batch init (instance inputs
     # host to device, FP64 tables), both schemes, every instance's prices back
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         h2d = sum(wl.L0.nbytes + wl.lam.nbytes + x.nbytes + W.nbytes + wl.strikes.nbytes for wl, x, W in inst)
         d2h = len(schemes) * sum(2 * 8 * wl.n * wl.strikes.shape[1] for wl in wls)
         ts = []
-        for _ in range(max(2, args.steps)):
+        for _ in range(max(2, steps)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             b2, keep2 = lll.lll_batch_init(inst)
@@ -311,7 +347,7 @@ def run_batch(args):
                        "lll_batch_prices of every instance + lll_batch_destroy"}
 
     cpu = None
-    if not args.no_cpu_baseline:
+    if with_cpu:
         from oracle import oracle as ora
         from oracle import quadrature
         threads = os.cpu_count() or 1
@@ -331,65 +367,50 @@ def run_batch(args):
                "sample": f"instances 0..{q - 1}, first min(paths, 512) paths each, {'+'.join(schemes)}; "
                          f"FP64 C oracle, {threads} threads, {dt:.1f} s"}
 
-    line = {"metric": METRIC, "value": value, "unit": "path·tenor·steps/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+    line = {"metric": METRIC, "value": value, "unit": "path·tenor·steps/s", "n_gpus": 1, "steps": steps,
+            "warmup": warmup, "ms_per_step": total_ms / steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"batch256: {len(wls)} uneven term structures (N 8..80, delta 0.25/0.5), "
                                    f"{sum(wl.paths for wl in wls)} paths in total, 11 strikes, "
                                    f"schemes={'+'.join(schemes)}, one persistent launch per scheme (CUDA graph)",
                        "global_paths": sum(wl.paths for wl in wls), "parallelism": "one GPU",
                        "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write outside the events)"},
-            "per_scheme": per, "caplets_per_s": caplets * len(schemes) * args.steps / (total_ms * 1e-3),
+            "per_scheme": per, "caplets_per_s": caplets * len(schemes) * steps / (total_ms * 1e-3),
             "roofline": roofline, "autotuned": tuned, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": 2 * len(schemes) * args.steps}
-    print(json.dumps(line), flush=True)
+            "gpu_launches": 2 * len(schemes) * steps}
     lll.lll_batch_destroy(b)
-    return 0
+    del flush
+    torch.cuda.empty_cache()
+    return line
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--paths", type=int, default=0, help="paths per GPU (default 2^20)")
-    ap.add_argument("--ref-paths", type=int, default=512, help="oracle paths per scheme per step")
-    ap.add_argument("--schemes", default="", help="default picard,full,mlp (large_single), picard,full (long_dated)")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-tune", action="store_true", help="library default launch shapes")
-    ap.add_argument("--mlp-kernel", default="auto", choices=["auto", "warp", "tc"],
-                    help="LLL_MLP kernel: tcgen05/TMEM (tc), mma.sync (warp) or the library's choice")
-    ap.add_argument("--launch", default="", help="fixed launch shape for the quadrature schemes: "
-                    "threads,blocks_per_sm,chunk_rows,paths_per_thread,lanes_per_path (no tuning)")
-    ap.add_argument("--workload", default="large_single", choices=["large_single", "long_dated", "batch256"],
-                    help="large_single: the N=40 term structure, 2^20 paths (default); long_dated: N=120, "
-                    "Q=96, 2^22 paths; batch256: 256 uneven term structures in one launch per scheme "
-                    "(Picard and full only)")
-    args = ap.parse_args()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "batch256":
-        return run_batch(args)
+def _alu_peaks(lll, torch, dev, rates=None):
+    """Roofline denominators of the non-tensor kernels, from the pipe rates the
+    library measures on this GPU (lll_measure_pipe_rates: results per SM per
+    clock) times the SM count and the maximum SM clock of MEASURED_PEAKS."""
+    rates = rates or lll.lll_measure_pipe_rates()
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    f = sms * sm_max * 1e6 / 1e12
+    return {"rates_per_sm_clock": rates, "sms": sms, "sm_max_mhz": sm_max,
+            "fp32": rates["ffma2_lane_ops"] * f, "fp32_nominal": 128 * f,
+            "fp32_basis": f"{sms} SMs x {rates['ffma2_lane_ops']:.1f} FP32 lane-ops/clk (packed FFMA2, measured "
+                          f"in this run by lll_measure_pipe_rates) x {sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS)",
+            "tanh": rates["tanh"] * f,
+            "tanh_basis": f"{sms} SMs x {rates['tanh']:.1f} tanh.approx/clk (measured in this run by "
+                          f"lll_measure_pipe_rates) x {sm_max:.0f} MHz"}
 
+
+def run_single(args, wl, schemes, steps, warmup, dev, rank, world, local, with_cpu=True, with_e2e=True,
+               rates=None, tune=True):
+    """One term structure: every scheme simulates all paths of the workload per
+    step.  Returns the JSON line (rank 0) or None."""
     import torch
     import torch.distributed as dist
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
-    from paper_1006_3340_gb300 import build as libbuild
-    libbuild.build()
     from paper_1006_3340_gb300 import lll
 
-    wl = _workload(args)
-    schemes = _schemes(args)
     hid, lay = _arch(wl)
     n, ns = wl.n, wl.strikes.shape[1]
     first = rank * wl.paths
@@ -400,6 +421,7 @@ def main():
     mlp_info = None
     mlp_params = None
     mlp_vec_params = None
+    mlp_oracle = None
     if "mlp" in schemes:
         # The learned compensator is trained once, on its own paths (seed 7),
         # with the project's GPU kernels; the timed steps then price with it.
@@ -409,11 +431,15 @@ def main():
                                  records_per_path=8, epochs=4, batch=8192, lr=2e-3, lr_final=1e-4, seed=7)
         torch.cuda.synchronize()
         lll.lll_mlp_set_kernel(sims["mlp"].ctx, args.mlp_kernel)
-        n_params, in_dim, in_pad, _ = lll.lll_mlp_layout(sims["mlp"].ctx, lay)
+        n_params, in_dim, in_pad, offs = lll.lll_mlp_layout(sims["mlp"].ctx, lay)
         mlp_params = lll.lll_mlp_params(sims["mlp"].ctx, 0, count=n_params)
         mlp_info = {"train_s": time.perf_counter() - t0, "final_loss_scaled": loss, "params": int(n_params),
+                    "s_y": float(mlp_params[1][4]),
                     "arch": f"{in_dim}->{hid}x{lay}->1 SiLU, BF16 weights, FP32 accumulate",
                     "train_pairs": "2^16 paths x 8 recorded steps x live rates (~1e7)"}
+        if with_cpu:
+            from oracle import mlp as omlp
+            mlp_oracle = (omlp.params_from_flat(mlp_params[0], offs, lay, hid, in_dim, in_pad), mlp_params[1], 0)
 
     if "mlp_vec" in schemes:
         # the vector-head network: one pass per path and step gives every rate's compensator
@@ -426,7 +452,7 @@ def main():
         nv, in_dim_v, _, _ = lll.lll_mlp_layout(sims["mlp_vec"].ctx, 3)
         mlp_vec_params = lll.lll_mlp_params(sims["mlp_vec"].ctx, 0, count=nv)
         mlp_info = dict(mlp_info or {}, vec={"train_s": time.perf_counter() - t0, "final_loss_scaled": lossv,
-                                              "params": int(nv),
+                                              "params": int(nv), "s_y": float(mlp_vec_params[1][4]),
                                               "arch": f"{in_dim_v}->128x3->48 SiLU (vector head), BF16, FP32 acc"})
 
     def one_step(evs=None):
@@ -446,14 +472,14 @@ def main():
             if s in ("picard", "full", "frozen"):
                 sims[s].set_launch(*shape)
                 tuned[s] = {"launch(threads,bps,chunk,ppt,lanes)": shape, "ms": None}
-    elif not args.no_tune:
+    elif tune:
         cands = [(128, 0, 0, 1, 1), (256, 0, 0, 1, 1), (128, 0, 0, 1, 2), (256, 0, 0, 1, 2)]
         for s in schemes:
             if s in ("picard", "full", "frozen"):
                 r = autotune.tune(sims[s], s, candidates=cands, repeats=2, use_cache=False)
                 tuned[s] = {"launch(threads,bps,chunk,ppt,lanes)": r["launch"], "ms": r["ms"]}
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         one_step()
     torch.cuda.synchronize()
 
@@ -466,7 +492,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("timed")  # profilers can select the timed launches
-    for k in range(args.steps):
+    for k in range(steps):
         flush.fill_(k & 0xFF)  # L2 flush between timed steps (outside the events)
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in schemes]
         one_step(evs)
@@ -489,7 +515,7 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     units_per_step = len(schemes) * wl.paths * wl.units_per_path() * world
-    value = units_per_step * args.steps / (total_ms * 1e-3)
+    value = units_per_step * steps / (total_ms * 1e-3)
 
     # per-scheme throughput and caplet prices of the last step
     per = {}
@@ -498,7 +524,7 @@ def main():
         kms, _ = sims[s].kernel_ms()
         p, se = sims[s].prices()
         per[s] = {"units_per_s": wl.paths * wl.units_per_path() / (ms * 1e-3), "ms": ms,
-                  "path_kernel_ms_last": kms, "atm_price_T10y": float(p[n - 1, ns // 2]),
+                  "path_kernel_ms_last": kms, "atm_price_last_maturity": float(p[n - 1, ns // 2]),
                   # one simulation prices every (maturity, strike) caplet of the term structure
                   "caplets_per_s": n * ns / (ms * 1e-3)}
     if "picard" in per and "full" in per:
@@ -511,24 +537,20 @@ def main():
         s1, s2, cnt = sims["picard"].sums()
         m1, m2, mcnt = shard.merge_sums(s1, s2, cnt)
         per["picard_merged_paths"] = mcnt
-        per["picard_merged_atm_T10y"] = float(m1[n - 1, ns // 2] / mcnt)
-    if "mlp_vec" in per and "full" in per:
-        pv, _ = sims["mlp_vec"].prices()
-        pf, _ = sims["full"].prices()
-        per["mlp_vec_vs_full_max_bp"] = float(np.abs(pv - pf).max() * 1e4)
-    if "mlp" in per and "full" in per:
-        pm, _ = sims["mlp"].prices()
-        pf, _ = sims["full"].prices()
-        per["mlp_vs_full_max_bp"] = float(np.abs(pm - pf).max() * 1e4)
+        per["picard_merged_atm_last_maturity"] = float(m1[n - 1, ns // 2] / mcnt)
+    for s in ("mlp", "mlp_vec"):
+        if s in per and "full" in per:
+            pv, _ = sims[s].prices()
+            pf, _ = sims["full"].prices()
+            per[f"{s}_vs_full_max_bp"] = float(np.abs(pv - pf).max() * 1e4)
 
     # Rooflines.  Quadrature kernels: 3Q FP32 lane-ops per unit (one FMA into
-    # A, one multiply w*E, one FMA into P) against 128 FP32 lanes per SM.
-    # MLP kernel: 2 x (multiply-adds of the network) per unit on the BF16
-    # tensor cores, against the measured sustained BF16 rate.
+    # A, one multiply w*E, one FMA into P) against the measured packed-FMA
+    # rate.  MLP kernels: one tanh.approx per SiLU against the measured MUFU
+    # rate (the binding pipe), with the tensor rate (2 x multiply-adds of the
+    # network) beside it against the measured sustained BF16 rate.
+    pk = _alu_peaks(lll, torch, dev, rates)
     peaks = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    fp32_peak = sms * 128 * sm_max * 1e6 / 1e12
     units = wl.paths * wl.units_per_path()
 
     def quad_roofline(s):
@@ -537,16 +559,12 @@ def main():
         shape = tuned.get(s, {}).get("launch(threads,bps,chunk,ppt,lanes)")
         lanes = shape[4] if shape and shape[4] else 1
         traffic = _traffic(f"{s}/QP{wl.Q}/lanes{lanes}") if wl.paths == 1 << 20 else None
-        r = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFP32-lane-op/s",
-             "frac": ach / fp32_peak, "traffic": traffic, "kernel": f"{s} path kernel, QP={wl.Q}",
-             "peak_basis": f"{sms} SMs x 128 FP32 lanes x {sm_max:.0f} MHz (sm_max_mhz of MEASURED_PEAKS)"}
+        r = {"bound": "alu", "achieved": ach, "peak": pk["fp32"], "unit": "TFP32-lane-op/s",
+             "frac": ach / pk["fp32"], "frac_of_nominal_128_lanes": ach / pk["fp32_nominal"], "traffic": traffic,
+             "kernel": f"{s} path kernel, QP={wl.Q}", "peak_basis": pk["fp32_basis"]}
         if clocks and clocks.get("sm_mhz"):
-            r["frac_at_sampled_clock"] = ach / (sms * 128 * clocks["sm_mhz"] * 1e6 / 1e12)
+            r["frac_at_sampled_clock"] = r["frac"] * pk["sm_max_mhz"] / clocks["sm_mhz"]
         return r
-
-    # MUFU (special function unit) rate of tanh.approx.f32, measured on this GPU by a
-    # probe: 16 per SM per clock (ex2 runs at 32); every SiLU of the network costs one.
-    sfu_peak = sms * 16 * sm_max * 1e6 / 1e12  # T tanh/s at the maximum SM clock
 
     def mlp_roofline(s="mlp"):
         """The learned drift: the binding pipe is MUFU (one tanh per SiLU), the
@@ -565,9 +583,8 @@ def main():
         bf16 = float(peaks.get("bf16_tflops_sustained", 1679.9))
         ach = silu / t / 1e12
         key = "mlp/L3/KT3" if args.mlp_kernel == "warp" else "mlp_tc/L3/KB1"
-        return {"bound": "alu", "pipe": "MUFU tanh.approx (SiLU)", "achieved": ach, "peak": sfu_peak,
-                "unit": "T tanh/s", "frac": ach / sfu_peak,
-                "peak_basis": f"{sms} SMs x 16 tanh/clk (probe on this GPU) x {sm_max:.0f} MHz",
+        return {"bound": "alu", "pipe": "MUFU tanh.approx (SiLU)", "achieved": ach, "peak": pk["tanh"],
+                "unit": "T tanh/s", "frac": ach / pk["tanh"], "peak_basis": pk["tanh_basis"],
                 "tensor_tflops": tflops, "tensor_frac": tflops / bf16,
                 "tensor_peak_basis": "bf16_tflops_sustained of MEASURED_PEAKS",
                 "traffic": _traffic(key) if (s == "mlp" and wl.paths == 1 << 20) else None,
@@ -582,7 +599,7 @@ def main():
     # end to end through the C ABI from host arrays: init (H2D of the model
     # inputs, FP64 tables on the GPU), strikes, each scheme, prices (D2H).
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         h2d = (wl.L0.nbytes + wl.lam.nbytes + x.nbytes + W.nbytes) * len(schemes) + wl.strikes.nbytes * len(schemes)
         if mlp_params is not None:
             h2d += mlp_params[0].nbytes + mlp_params[1].nbytes
@@ -590,7 +607,7 @@ def main():
             h2d += mlp_vec_params[0].nbytes + mlp_vec_params[1].nbytes
         d2h = len(schemes) * 2 * n * ns * 8
         ts = []
-        for k in range(max(2, args.steps)):
+        for k in range(max(2, steps)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for s in schemes:
@@ -620,12 +637,13 @@ def main():
                "note": "per scheme: lll_init + lll_set_strikes (+ network parameters for mlp) + lll_simulate + lll_price_caplets + lll_destroy"}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl, schemes)
+    if rank == 0 and world == 1 and with_cpu:
+        cpu = cpu_baseline(wl, schemes, mlp=mlp_oracle)
 
+    line = None
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "path·tenor·steps/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+                "steps": steps, "warmup": warmup, "ms_per_step": total_ms / steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": _describe(wl, schemes), "global_paths": wl.paths * world,
@@ -633,12 +651,88 @@ def main():
                            f"({L2_FLUSH_BYTES >> 20} MiB write outside the events)"},
                 "per_scheme": per, "roofline": roofline,
                 "roofline_picard": quad_roofline("picard") if "picard" in schemes else None,
+                "roofline_mlp": mlp_roofline("mlp") if "mlp" in schemes else None,
                 "roofline_mlp_vec": mlp_roofline("mlp_vec") if "mlp_vec" in schemes else None,
+                "measured_pipe_rates_per_sm_clock": pk["rates_per_sm_clock"],
                 "mlp": mlp_info, "autotuned": tuned, "cpu_baseline": cpu, "e2e": e2e,
-                "clocks": clocks, "gpu_launches": 2 * len(schemes) * args.steps}
-        print(json.dumps(line), flush=True)
+                "clocks": clocks, "gpu_launches": 2 * len(schemes) * steps}
     for s in sims.values():
         s.close()
+    del flush
+    torch.cuda.empty_cache()
+    return line
+
+
+def _extra_block(line):
+    """The figures of another configuration kept in the headline line."""
+    keep = ("value", "unit", "ms_per_step", "steps", "warmup", "config", "per_scheme", "caplets_per_s",
+            "roofline", "roofline_picard", "roofline_mlp", "autotuned", "clocks", "mlp")
+    return {k: line[k] for k in keep if k in line}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--paths", type=int, default=0, help="paths per GPU (default 2^20)")
+    ap.add_argument("--ref-paths", type=int, default=512, help="oracle paths per scheme per step")
+    ap.add_argument("--schemes", default="", help="default picard,full,mlp (large_single), picard,full (long_dated)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="library default launch shapes")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default run: leave out the batch256 and long_dated blocks")
+    ap.add_argument("--mlp-kernel", default="auto", choices=["auto", "warp", "tc"],
+                    help="LLL_MLP kernel: tcgen05/TMEM (tc), mma.sync (warp) or the library's choice")
+    ap.add_argument("--launch", default="", help="fixed launch shape for the quadrature schemes: "
+                    "threads,blocks_per_sm,chunk_rows,paths_per_thread,lanes_per_path (no tuning)")
+    ap.add_argument("--workload", default="large_single", choices=["large_single", "long_dated", "batch256"],
+                    help="large_single: the N=40 term structure, 2^20 paths (default); long_dated: N=120, "
+                    "Q=96, 2^22 paths; batch256: 256 uneven term structures in one launch per scheme "
+                    "(Picard and full only)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.workload == "batch256" and world > 1:
+        print(json.dumps({"error": "--workload batch256 runs on one GPU"}), flush=True)
+        return 1
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_1006_3340_gb300 import build as libbuild
+    libbuild.build()
+    from paper_1006_3340_gb300 import lll
+
+    rates = lll.lll_measure_pipe_rates()
+    if args.workload == "batch256":
+        line = run_batch(args, args.steps, args.warmup, not args.no_cpu_baseline, not args.no_e2e, rates)
+    else:
+        wl = _workload(args)
+        line = run_single(args, wl, _schemes(args), args.steps, args.warmup, dev, rank, world, local,
+                          with_cpu=not args.no_cpu_baseline, with_e2e=not args.no_e2e, rates=rates,
+                          tune=not args.no_tune)
+        if (line is not None and world == 1 and args.workload == "large_single" and not args.no_extra
+                and not args.paths):
+            # the other single-GPU configurations, a few steps each, in the same line
+            extra = {"batch256": _extra_block(run_batch(args, 2, 1, False, False, rates))}
+            wl5 = workloads.long_dated()
+            extra["long_dated"] = _extra_block(run_single(
+                args, wl5, ["picard", "full"], 2, 1, dev, rank, world, local, with_cpu=False, with_e2e=False,
+                rates=rates, tune=True))
+            line["extra_configs"] = extra
+    if line is not None:
+        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0

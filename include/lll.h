@@ -171,8 +171,11 @@ int lll_kernel_ms(lll_ctx *ctx, float *path_kernel_ms, float *simulate_ms);
  * memory at start-up through their own pool, and latency-bound callers that
  * cannot afford the device-wide synchronisation cudaMalloc / cudaFree may
  * imply.  (The paper has no counterpart: this is an engineering entry point.)
- *   ctx, scheme, first_path, paths, seed: as for lll_simulate (snapshots are
- *                not recorded).
+ *   ctx, first_path, paths, seed: as for lll_simulate (snapshots are not
+ *                recorded).
+ *   scheme     : LLL_FULL, LLL_PICARD or LLL_FROZEN; LLL_MLP, LLL_EXPAND1 and
+ *                LLL_EXPAND2 return LLL_EUNSUPPORTED (their kernels keep
+ *                per-context buffers), any other value LLL_EINVAL.
  *   d_sums     : caller-owned device buffer of n * n_strikes * 2 doubles,
  *                d_sums[2*(m*n_strikes + q)] = sum of payoffs and [... + 1] =
  *                sum of squared payoffs of maturity m+1, strike q.
@@ -180,8 +183,12 @@ int lll_kernel_ms(lll_ctx *ctx, float *path_kernel_ms, float *simulate_ms);
  * Scratch (per-block path state and payoff partials) comes from one static
  * 32 MiB device array that every GPU loading the library holds until exit;
  * a launch needing more returns LLL_EUNSUPPORTED with the byte counts in
- * lll_last_error.  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * lll_last_error.  Each call made outside a stream capture looks the array's
+ * address up (cudaGetSymbolAddress), so a module reloaded after
+ * cudaDeviceReset is found at its new address; a call made while the
+ * context's stream is captured uses the address the last uncaptured call
+ * found on that device, so make one uncaptured call first (a captured first
+ * call returns LLL_ESTATE).
  * All calls share the array: calls that overlap on the GPU (other streams,
  * other threads, other contexts on the same device) race and corrupt each
  * other's results; serialise them.  Nothing in the array needs clearing
@@ -239,6 +246,18 @@ int lll_batch_simulate(lll_batch *b, int scheme, uint64_t seed);
 /* lll_batch_prices -- caplet prices and standard errors of instance q
  * ([n_q][n_strikes_q]).  Synchronises the stream. */
 int lll_batch_prices(lll_batch *b, int q, double *prices, double *stderr_);
+
+/* lll_batch_set_snapshots -- parity snapshots of instance q, as
+ * lll_set_snapshots does for one context: log L_l(T_m) (l >= m) of `count`
+ * paths of that instance, those whose index is a multiple of `stride`,
+ * recorded by every following lll_batch_simulate (count = 0 disables).
+ * Allocates the instance's snapshot buffer; synchronises the stream. */
+int lll_batch_set_snapshots(lll_batch *b, int q, uint64_t count, uint64_t stride);
+
+/* lll_batch_get_paths -- snapshots of instance q from the last batch
+ * simulation, laid out as lll_get_paths: out[(p*n_q + (m-1))*n_q + (l-1)],
+ * recorded snapshot p = path p*stride of the instance.  Synchronises. */
+int lll_batch_get_paths(lll_batch *b, int q, uint64_t first, uint64_t count, float *out);
 
 /* lll_batch_kernel_ms -- device time of the last lll_batch_simulate. */
 int lll_batch_kernel_ms(lll_batch *b, float *ms);
@@ -334,6 +353,29 @@ int lll_mlp_set_kernel(lll_ctx *ctx, int kind);
 #define LLL_INJECT_NONE 0
 #define LLL_INJECT_MMA_STALL 1
 int lll_inject(lll_ctx *ctx, int what);
+
+/* ---- Measuring calls -------------------------------------------------------
+ * lll_philox_words -- the device Philox-4x32-10 of every path kernel (Salmon
+ * et al., SC'11; the generator behind the driver increments of Section 4)
+ * evaluated on caller counters, for bit-exact checks of the integer stream:
+ *   ctr  : [count][4] host counters (word 0 .. word 3; the path kernels use
+ *          (step, instance, path_lo, path_hi)),
+ *   seed : key (seed_lo, seed_hi),
+ *   out  : [count][4] host output words.
+ * count in [1, 2^24].  Allocates and frees device memory on the current
+ * device and synchronises it. */
+int lll_philox_words(const uint32_t *ctr, uint64_t count, uint64_t seed, uint32_t *out);
+
+/* lll_measure_pipe_rates -- results per SM per clock of the instructions the
+ * rooflines are stated in, measured on the current device (one block of 32
+ * warps per SM, 8 independent chains per thread, SM cycle counter; median
+ * over the SMs).  rates[0] tanh.approx.f32, [1] ex2.approx.ftz.f32,
+ * [2] rcp.approx.ftz.f32, [3] FP32 lane-ops of packed fma.rn.f32x2 (two per
+ * lane), [4] FP32 lane-ops of scalar fma.rn.f32; the first `count` (1..5)
+ * are measured.  Takes a few milliseconds; synchronises the device.  The
+ * paper has no counterpart: the numbers are the denominators of the
+ * benchmark's roofline fractions. */
+int lll_measure_pipe_rates(double *rates, int count);
 
 /* lll_mlp_save / lll_mlp_load -- flat binary file: magic, (hidden, layers,
  * in_dim, N), the five scales, parameter count, FP32 parameters. */

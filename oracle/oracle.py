@@ -204,3 +204,30 @@ def discount_terminal(wl) -> float:
 
 def discount(wl, k: int) -> float:
     return float(np.prod(1.0 / (1.0 + wl.delta * np.asarray(wl.L0[:k]))))
+
+
+def swaption_prices(wl, snap, strikes=None):
+    """Co-terminal payer swaptions priced on simulated paths (Section 1 names
+    swaptions as the multi-LIBOR products without closed forms).
+
+    The swaption expiring at T_m exercises into the swap over [T_m, T_N]:
+    fixed rate K against L, both legs paying at T_{m+1} .. T_N.  Its value at
+    T_m, written with the bond prices of that date,
+        B(T_m, T_j) = prod_{l=m}^{j-1} 1 / (1 + delta L_l(T_m)),
+    is V_m = (1 - B(T_m, T_N) - K delta sum_{j=m+1}^{N} B(T_m, T_j))^+.  Under
+    the terminal measure its price is B(0, T_N) E[V_m / B(T_m, T_N)].
+
+    snap[p, m-1, l-1] = log L_l(T_m) (l >= m) of the paths; strikes [n][ns].
+    Returns prices [n][ns]."""
+    n, d = wl.N - 1, wl.delta
+    strikes = np.asarray(wl.strikes if strikes is None else strikes, dtype=np.float64)
+    BN = discount_terminal(wl)
+    out = np.zeros((n, strikes.shape[1]))
+    for m in range(1, n + 1):
+        L = np.exp(np.asarray(snap[:, m - 1, m - 1:], dtype=np.float64))  # L_m .. L_n at T_m
+        # B(T_m, T_j) for j = m+1 .. N: running product of the discount factors
+        bonds = np.cumprod(1.0 / (1.0 + d * L), axis=1)
+        for q in range(strikes.shape[1]):
+            V = np.maximum(1.0 - bonds[:, -1] - strikes[m - 1, q] * d * bonds.sum(axis=1), 0.0)
+            out[m - 1, q] = BN * np.mean(V / bonds[:, -1])
+    return out

@@ -287,6 +287,14 @@ int lll_batch_simulate(lll_batch *b, int scheme, uint64_t seed)
         rc = plan_launch(b->inst[q], scheme, 0, b->paths[q], seed, &plan);
         if (rc != LLL_OK) return berr(b, rc, std::string("instance plan: ") + lll_last_error(b->inst[q]));
         plan.args.inst = (uint32_t)q; // Philox counter word 1: instances draw independent streams
+        lll_ctx *c = b->inst[q];
+        if (c->d_snap) { // parity snapshots of this instance (lll_batch_set_snapshots)
+            plan.args.snap = c->d_snap;
+            plan.args.snap_stride = c->snap_stride;
+            plan.args.snap_pitch = c->n_snap;
+            plan.args.n_snap = std::min<uint64_t>(c->n_snap, (b->paths[q] + c->snap_stride - 1) / c->snap_stride);
+        }
+        c->last_snap_paths = plan.args.n_snap;
         b->h_desc[q] = plan.args;
     }
     cudaStream_t st = b->stream;
@@ -321,6 +329,28 @@ int lll_batch_simulate(lll_batch *b, int scheme, uint64_t seed)
     if (e == cudaSuccess) e = cudaEventRecord(b->ev[1], st);
     if (e != cudaSuccess) return berr(b, LLL_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
     b->simulated = true;
+    for (lll_ctx *c : b->inst) c->simulated = c->d_snap != nullptr; // snapshots readable
+    return LLL_OK;
+}
+
+int lll_batch_set_snapshots(lll_batch *b, int q, uint64_t count, uint64_t stride)
+{
+    if (!b) return berr(nullptr, LLL_EINVAL, "batch is NULL");
+    if (q < 0 || q >= (int)b->inst.size()) return berr(b, LLL_EINVAL, "bad instance");
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return berr(b, LLL_ECUDA, "stream synchronize");
+    const int rc = lll_set_snapshots(b->inst[q], count, stride);
+    if (rc != LLL_OK) return berr(b, rc, lll_last_error(b->inst[q]));
+    b->inst[q]->simulated = false;
+    return LLL_OK;
+}
+
+int lll_batch_get_paths(lll_batch *b, int q, uint64_t first, uint64_t count, float *out)
+{
+    if (!b) return berr(nullptr, LLL_EINVAL, "batch is NULL");
+    if (q < 0 || q >= (int)b->inst.size()) return berr(b, LLL_EINVAL, "bad instance");
+    if (!b->simulated) return berr(b, LLL_ESTATE, "no batch simulation to read");
+    const int rc = lll_get_paths(b->inst[q], first, count, out);
+    if (rc != LLL_OK) return berr(b, rc, lll_last_error(b->inst[q]));
     return LLL_OK;
 }
 

@@ -101,7 +101,8 @@ int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, u
 {
     if (!ctx) return fail(nullptr, LLL_EINVAL, "ctx is NULL");
     if (!plan) return fail(ctx, LLL_EINVAL, "plan is NULL");
-    if (scheme == LLL_MLP) return fail(ctx, LLL_EUNSUPPORTED, "LLL_MLP runs through lll_simulate only");
+    if (scheme == LLL_MLP || scheme == LLL_EXPAND1 || scheme == LLL_EXPAND2)
+        return fail(ctx, LLL_EUNSUPPORTED, "LLL_MLP and LLL_EXPAND1/2 run through lll_simulate only");
     if (scheme != LLL_FULL && scheme != LLL_PICARD && scheme != LLL_FROZEN)
         return fail(ctx, LLL_EINVAL, "unknown scheme");
     if (ctx->ns == 0) return fail(ctx, LLL_ESTATE, "lll_set_strikes must come before simulating");

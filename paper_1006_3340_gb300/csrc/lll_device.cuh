@@ -1,9 +1,9 @@
 // lll_device.cuh -- device-side random numbers and driver increments.
 //
 // Philox-4x32-10: Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as
-// easy as 1, 2, 3" (SC'11).  The NIG increment (Section 4 of the paper: the
-// driver is NIG, drawn "by the standard methodology") is a normal
-// variance-mean mixture beta V + sqrt(V) Z + mu h with V ~ IG(mean m, shape l),
+// easy as 1, 2, 3" (SC'11).  The NIG increment (Section 4 of the paper draws
+// its NIG driver by the usual normal variance-mean mixture, without detail)
+// is beta V + sqrt(V) Z + mu h with V ~ IG(mean m, shape l),
 // m = dbar h / gamma, l = (dbar h)^2; V by Michael, Schucany & Haas (1976).
 #pragma once
 

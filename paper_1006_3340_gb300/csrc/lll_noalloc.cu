@@ -11,8 +11,11 @@
 // path kernel) lives in the file-scope array below: kScratchBytes on every
 // GPU that loads the library, held until the process exits.  Host code must
 // not use the array's name as a device address (on the host it names a
-// stand-in object); the device address is looked up once per device with
-// cudaGetSymbolAddress and cached.
+// stand-in object); the device address comes from cudaGetSymbolAddress.  It
+// is looked up again on every call made outside a stream capture (after a
+// cudaDeviceReset the module, and with it the array, may be reloaded at
+// another address); a call made during a capture, when the lookup is not
+// allowed, uses the address the last uncaptured call found on that device.
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -33,16 +36,20 @@ std::mutex g_mu;
 void *g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch array on `device` (which must be current).
-cudaError_t scratch_address(int device, void **out)
+// capturing: the caller's stream is being captured, so only the address an
+// earlier uncaptured call found may be used (cudaErrorStreamCaptureUnsupported
+// if there is none).
+cudaError_t scratch_address(int device, bool capturing, void **out)
 {
     if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[device]) {
+    if (!capturing) {
         void *ptr = nullptr;
         const cudaError_t e = cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_addr[device] = ptr;
     }
+    if (!g_scratch_addr[device]) return cudaErrorStreamCaptureUnsupported;
     *out = g_scratch_addr[device];
     return cudaSuccess;
 }
@@ -74,8 +81,15 @@ extern "C" int lll_simulate_noalloc(lll_ctx *ctx, int scheme, uint64_t first_pat
     cudaError_t e = cudaGetDevice(&current);
     if (e != cudaSuccess || current != plan.device)
         return record_error(ctx, LLL_ECUDA, "the context's device must be current");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(plan.stream, &cap);
+    const bool capturing = e != cudaSuccess || cap != cudaStreamCaptureStatusNone;
+    if (e != cudaSuccess) cudaGetLastError(); // keep the launch check below from seeing this query's error
     void *base = nullptr;
-    e = scratch_address(current, &base);
+    e = scratch_address(current, capturing, &base);
+    if (e == cudaErrorStreamCaptureUnsupported)
+        return record_error(ctx, LLL_ESTATE,
+                            "lll_simulate_noalloc: make one call outside stream capture first on this device");
     if (e != cudaSuccess) {
         std::string msg = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
         return record_error(ctx, LLL_ECUDA, msg.c_str());

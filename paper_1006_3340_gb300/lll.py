@@ -93,12 +93,16 @@ def load():
         "lll_mlp_load": (I, [V, ctypes.c_char_p]),
         "lll_mlp_set_kernel": (I, [V, I]),
         "lll_inject": (I, [V, I]),
+        "lll_philox_words": (I, [V, U64, U64, V]),
+        "lll_measure_pipe_rates": (I, [_dp, I]),
         "lll_batch_init": (I, [ctypes.POINTER(V), I, ctypes.POINTER(lll_instance), V]),
         "lll_batch_set_launch": (I, [V, I, I, I]),
         "lll_batch_use_graph": (I, [V, I]),
         "lll_batch_simulate": (I, [V, I, U64]),
         "lll_batch_prices": (I, [V, I, _dp, _dp]),
         "lll_batch_kernel_ms": (I, [V, _fp]),
+        "lll_batch_set_snapshots": (I, [V, I, U64, U64]),
+        "lll_batch_get_paths": (I, [V, I, U64, U64, _fp]),
         "lll_batch_destroy": (None, [V]),
         "lll_last_error": (ctypes.c_char_p, [V]),
         "lll_destroy": (None, [V]),
@@ -333,6 +337,17 @@ def lll_batch_prices(b, q, n, ns):
     return p, se
 
 
+def lll_batch_set_snapshots(b, q, count, stride=1):
+    _check(load().lll_batch_set_snapshots(b, int(q), int(count), int(stride)))
+
+
+def lll_batch_get_paths(b, q, n, first, count):
+    """log L_l(T_m) of recorded snapshots [first, first+count) of instance q: [count, n, n]."""
+    out = np.zeros((count, n, n), dtype=np.float32)
+    _check(load().lll_batch_get_paths(b, int(q), int(first), int(count), out.ctypes.data_as(_fp)))
+    return out
+
+
 def lll_batch_kernel_ms(b):
     ms = ctypes.c_float()
     _check(load().lll_batch_kernel_ms(b, ctypes.byref(ms)))
@@ -342,6 +357,24 @@ def lll_batch_kernel_ms(b):
 def lll_batch_destroy(b):
     if b:
         load().lll_batch_destroy(b)
+
+
+def lll_philox_words(counters, seed):
+    """Device Philox-4x32-10 output words [count][4] (uint32) for counters [count][4]."""
+    ctr = np.ascontiguousarray(counters, dtype=np.uint32).reshape(-1, 4)
+    out = np.zeros_like(ctr)
+    _check(load().lll_philox_words(ctr.ctypes.data, ctr.shape[0], int(seed) & (2 ** 64 - 1), out.ctypes.data))
+    return out
+
+
+PIPE_RATE_NAMES = ("tanh", "ex2", "rcp", "ffma2_lane_ops", "ffma_lane_ops")
+
+
+def lll_measure_pipe_rates(count=5):
+    """Measured results per SM per clock: {name: rate} (see include/lll.h)."""
+    r = np.zeros(count)
+    _check(load().lll_measure_pipe_rates(_d(r), int(count)))
+    return {k: float(v) for k, v in zip(PIPE_RATE_NAMES, r)}
 
 
 def lll_last_error(ctx=None) -> str:

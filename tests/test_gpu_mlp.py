@@ -193,27 +193,36 @@ def test_tcgen05_kernel_matches_mma_sync_kernel(lll, trained):
     assert np.abs(p_tr - p_wr).max() <= 2e-8
 
 
+# Paths compared with the FP64 oracle one by one: two CTAs of the tensor-
+# memory kernel (two 128-row tiles each, all four TMEM lane quadrants and
+# every epilogue warp) and a third CTA with a ragged 37-path tile; for the
+# mma.sync kernel 17 warps of 32 paths and a ragged one.
+ORACLE_PATHS = 2 * 256 + 37
+
+
 @pytest.fixture(scope="module")
 def fp64_scheme(lll, trained):
-    """The FP64 oracle of the scheme with the trained network, first 24 paths."""
+    """The FP64 oracle of the scheme with the trained network, first ORACLE_PATHS paths."""
     wl, x, W, sim, loss = trained
     n_params, in_dim, in_pad, offs = lll.lll_mlp_layout(sim.ctx, L)
     flat, scales = lll.lll_mlp_params(sim.ctx, 0, count=n_params)
     params = omlp.params_from_flat(flat, offs, L, H, in_dim, in_pad)
-    return scales, omlp.simulate_scheme(ora.OracleModel(wl, x, W), params, scales, npaths=24)
+    return scales, omlp.simulate_scheme(ora.OracleModel(wl, x, W), params, scales, npaths=ORACLE_PATHS)
 
 
 @pytest.mark.parametrize("kind", ["tc", "warp", "layered"])
 def test_mlp_kernels_match_fp64_scheme_path_by_path(lll, trained, fp64_scheme, kind):
-    """Both LLL_MLP kernels against the FP64 oracle of the same scheme with the
-    same (BF16-stored) network, on identical Philox increments.  The GPU feeds
-    BF16 features and activations through the network, so one evaluation of f
-    may differ from the FP64 one by a few per cent of its unit RMS (the forward
+    """Every LLL_MLP kernel against the FP64 oracle of the same scheme with the
+    same (BF16-stored) network, on identical Philox increments, path by path
+    over both tiles of two CTAs and a ragged third.  The GPU feeds BF16
+    features and activations through the network, so one evaluation of f may
+    differ from the FP64 one by a few per cent of its unit RMS (the forward
     test's bound, 2e-2 of max |f|, plus the SiLU approximation); a log-rate
     offset integrates h s_y times that over at most T_N / h steps:
-    |d log L| <= T_N s_y 0.05."""
+    |d log L| <= T_N s_y 0.05.  The median error must sit far below that
+    bound (rounding errors of single evaluations do not add up coherently)."""
     wl, x, W, sim, loss = trained
-    cnt = 24
+    cnt = ORACLE_PATHS
     scales, ref = fp64_scheme
     try:
         lll.lll_mlp_set_kernel(sim.ctx, kind)
@@ -225,8 +234,13 @@ def test_mlp_kernels_match_fp64_scheme_path_by_path(lll, trained, fp64_scheme, k
     mask = ~np.isnan(ref["snap"])
     assert np.array_equal(mask, ~np.isnan(z))
     tol = wl.N * wl.delta * float(scales[4]) * 0.05
-    err = np.abs(z[mask] - ref["snap"][mask]).max()
+    d = np.abs(z - ref["snap"])
+    err = d[mask].max()
     assert err <= tol, (err, tol)
+    # every path, tile and lane quadrant meets the bound (not only the worst)
+    per_path = np.nanmax(d.reshape(cnt, -1), axis=1)
+    assert np.all(per_path <= tol), np.argmax(per_path)
+    assert np.median(per_path) <= 0.25 * tol, (np.median(per_path), tol)
     # payoff sensitivity to a log-rate: delta B(0,T_N) L (1 + delta L)^n < 1e-2
     assert np.abs(p - ref["price"]).max() <= 1e-2 * tol
 

@@ -109,13 +109,22 @@ def fp64_vec(lll, trained_vec):
     flat, scales = lll.lll_mlp_params(sim.ctx, 0, count=n_params)
     _, O = lll.lll_mlp_shape(sim.ctx)
     params = omlp.params_from_flat(flat, offs, L, H, in_dim, in_pad, outputs=O)
-    return scales, omlp.simulate_scheme(ora.OracleModel(wl, x, W), params, scales, npaths=64, head=1)
+    return scales, omlp.simulate_scheme(ora.OracleModel(wl, x, W), params, scales, npaths=ORACLE_PATHS,
+                                        head=1)
+
+
+# Two CTAs of the tensor-memory kernel (both 128-row tiles, every TMEM lane
+# quadrant and column quarter) and a ragged 37-path third.
+ORACLE_PATHS = 2 * 256 + 37
 
 
 @pytest.mark.parametrize("kind", ["tc", "layered"])
 def test_vector_head_matches_fp64_scheme_path_by_path(lll, trained_vec, fp64_vec, kind):
+    """Path by path against the FP64 oracle of the vector-head scheme over
+    every tile, lane quadrant and column quarter of two CTAs and a ragged
+    third; bound T_N s_y 0.05 on each log-rate (see the per-rate test)."""
     wl, x, W, sim, loss = trained_vec
-    cnt = 64
+    cnt = ORACLE_PATHS
     scales, ref = fp64_vec
     try:
         lll.lll_mlp_set_kernel(sim.ctx, kind)
@@ -127,8 +136,11 @@ def test_vector_head_matches_fp64_scheme_path_by_path(lll, trained_vec, fp64_vec
     mask = ~np.isnan(ref["snap"])
     assert np.array_equal(mask, ~np.isnan(z))
     tol = wl.N * wl.delta * float(scales[4]) * 0.05
-    err = np.abs(z[mask] - ref["snap"][mask]).max()
-    assert err <= tol, (err, tol)
+    d = np.abs(z - ref["snap"])
+    assert d[mask].max() <= tol, (d[mask].max(), tol)
+    per_path = np.nanmax(d.reshape(cnt, -1), axis=1)
+    assert np.all(per_path <= tol), np.argmax(per_path)
+    assert np.median(per_path) <= 0.25 * tol, (np.median(per_path), tol)
     assert np.abs(p - ref["price"]).max() <= 1e-2 * tol
 
 

@@ -1,9 +1,9 @@
 """Co-terminal payer swaptions (lll_set_product(LLL_PRODUCT_SWAPTION)) on the
 same simulated paths as the caplets.
 
-* Against the FP64 oracle: the swaption payoff evaluated on the oracle's own
-  log-rates at each expiry (snapshots of the same Philox paths) must give the
-  GPU's prices within 1e-7 for the quadrature schemes.
+* Against the FP64 oracle: the oracle's swaption prices (oracle.swaption_prices,
+  bond prices at each expiry from its own log-rates of the same Philox paths)
+  must equal the GPU's within 1e-7 for the quadrature schemes.
 * At the last expiry the swap has one period, so the swaption is the last
   caplet: equal prices on the same paths (to the FP32 rounding of the caplet
   payoff).
@@ -34,23 +34,6 @@ def lll():
     return mod
 
 
-def _swaption_prices_from_snapshots(wl, snap, strikes):
-    """B(0,T_N) mean of ((1 + delta L_m) P - 1 - K delta S)^+ per expiry and strike."""
-    n, d = wl.n, wl.delta
-    BN = ora.discount_terminal(wl)
-    out = np.zeros((n, strikes.shape[1]))
-    for m in range(1, n + 1):
-        L = np.exp(snap[:, m - 1, m - 1:])          # L_m .. L_n at T_m
-        f = 1.0 + d * L
-        suffix = np.cumprod(f[:, ::-1], axis=1)[:, ::-1]  # prod_{l>=j}, j = m..n
-        P = suffix[:, 1] if n > m else np.ones(len(L))  # prod_{l>m}
-        S = 1.0 + (suffix[:, 1:].sum(axis=1) if n > m else 0.0)
-        for q in range(strikes.shape[1]):
-            X = f[:, 0] * P - 1.0 - strikes[m - 1, q] * d * S
-            out[m - 1, q] = BN * np.maximum(X, 0.0).mean()
-    return out
-
-
 @pytest.mark.parametrize("scheme,code", [("full", ora.FULL), ("picard", ora.PICARD)])
 def test_swaptions_match_oracle_paths(lll, scheme, code):
     wl = workloads.large_single(paths=2048)
@@ -63,7 +46,7 @@ def test_swaptions_match_oracle_paths(lll, scheme, code):
     finally:
         sim.close()
     ref = ora.simulate(ora.OracleModel(wl, x, W), code, want_snap=True)
-    want = _swaption_prices_from_snapshots(wl, ref["snap"], wl.strikes)
+    want = ora.swaption_prices(wl, ref["snap"], wl.strikes)
     assert np.abs(p - want).max() <= 1e-7
 
 

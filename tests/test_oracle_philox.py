@@ -1,12 +1,13 @@
 """Pins of the oracle's Philox-4x32-10 and uniform mapping.
 
 External pin: cuRAND's host-side Philox4_32_10 generator (a CPU
-implementation shipped with CUDA, run as a black box).  Its output group g
-is Philox-4x32-10 of counter (g div 2^16, 0, g mod 2^16, 0) under key
-(seed_lo, seed_hi); the oracle must reproduce every word bit for bit.  The
-path kernels use counter (step, instance, path_lo, path_hi), so for one
-instance and fewer than 2^32 paths every draw they make sits in the pinned
-(word 0, word 2) plane.
+implementation shipped with CUDA, run as a black box).  Its output group G
+(counting from the generator offset divided by 4) is Philox-4x32-10 of the
+counter (G div 2^16 mod 2^32, G div 2^48, G mod 2^16, 0) under key
+(seed_lo, seed_hi); the oracle must reproduce every word bit for bit.  With
+offsets beyond 2^50 words this reaches counter word 1 (the batched launch's
+instance word), including the carry out of word 0.  Word 3 (path_hi) is
+pinned on the GPU through cuRAND's device API (tests/test_gpu_philox.py).
 """
 import ctypes
 import ctypes.util
@@ -35,7 +36,7 @@ def _curand():
     return None
 
 
-def _curand_host_stream(seed: int, n_groups: int) -> np.ndarray:
+def _curand_host_stream(seed: int, n_groups: int, offset: int = 0) -> np.ndarray:
     lib = _curand()
     if lib is None:
         pytest.skip("libcurand not available")
@@ -44,6 +45,8 @@ def _curand_host_stream(seed: int, n_groups: int) -> np.ndarray:
         pytest.skip("cuRAND host generator unavailable")
     try:
         assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        if offset:
+            assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(offset)) == 0
         out = np.zeros(4 * n_groups, dtype=np.uint32)
         assert lib.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p),
                                   ctypes.c_size_t(out.size)) == 0
@@ -64,6 +67,23 @@ def test_philox_matches_curand_host_generator(seed):
         g = int(g)
         got = oracle.philox((g >> 16, 0, g & 0xFFFF, 0), key)
         assert got == [int(v) for v in ref[g]], (seed, g)
+
+
+@pytest.mark.parametrize("seed", [42, 0xFEDCBA9876543210])
+@pytest.mark.parametrize("first_group", [(1 << 48) + (5 << 16) + 7,          # word 1 = 1
+                                         (3 << 48) + (0xFFFFFFFF << 16) + 0xFFF0,  # carry word 0 -> 1
+                                         (0x3FFF << 48) + (0x89ABCDEF << 16)])      # word 1 = 2^14 - 1
+def test_philox_counter_word_1_matches_curand_offset_stream(seed, first_group):
+    n_groups = 64
+    ref = _curand_host_stream(seed, n_groups, offset=4 * first_group)
+    key = (seed & 0xFFFFFFFF, seed >> 32)
+    words1 = set()
+    for g in range(n_groups):
+        G = first_group + g
+        ctr = ((G >> 16) & 0xFFFFFFFF, G >> 48, G & 0xFFFF, 0)
+        words1.add(ctr[1])
+        assert oracle.philox(ctr, key) == [int(v) for v in ref[g]], (seed, hex(G))
+    assert min(words1) > 0
 
 
 def test_philox_uses_every_counter_and_key_word():

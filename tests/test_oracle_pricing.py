@@ -134,3 +134,26 @@ def test_schemes_share_random_numbers_and_are_deterministic():
     assert np.allclose(a["sum"], b["sum"], rtol=1e-13, atol=0)
     c = _run(wl, oracle.PICARD, threads=7)
     assert np.array_equal(b["sum"], c["sum"])
+
+
+def test_swaption_oracle_last_expiry_is_last_caplet_and_zero_strike_is_forward_bond():
+    """A co-terminal swaption with one period left is the last caplet on the
+    same paths; with strike 0 its deflated payoff is 1 / B(T_m, T_N) - 1,
+    whose terminal-measure mean is B(0, T_m) / B(0, T_N) - 1 (deflated bond
+    prices are martingales), so the price is B(0, T_m) - B(0, T_N)."""
+    wl = workloads.small_plain(paths=20000)
+    x, W = quadrature.rule_for(wl)
+    r = oracle.simulate(oracle.OracleModel(wl, x, W), oracle.FULL, want_snap=True)
+    swp = oracle.swaption_prices(wl, r["snap"], wl.strikes)
+    assert abs(swp[-1, 0] - r["price"][-1, 0]) <= 1e-15
+    assert np.all(swp[:-1, 0] > r["price"][:-1, 0])
+    zero = oracle.swaption_prices(wl, r["snap"], np.zeros((wl.n, 1)))[:, 0]
+    want = np.array([oracle.discount(wl, m) - oracle.discount_terminal(wl) for m in range(1, wl.n + 1)])
+    # the same path average of B(0,T_N) (prod_{l>=m}(1 + delta L_l) - 1): compare
+    # against its standard error
+    BN = oracle.discount_terminal(wl)
+    for m in range(1, wl.n + 1):
+        L = np.exp(r["snap"][:, m - 1, m - 1:])
+        v = BN * (np.prod(1.0 + wl.delta * L, axis=1) - 1.0)
+        assert abs(zero[m - 1] - v.mean()) <= 1e-14
+        assert abs(zero[m - 1] - want[m - 1]) <= 3 * v.std() / np.sqrt(len(v)), m
