@@ -470,14 +470,16 @@ def run_single(args, wl, schemes, steps, warmup, dev, rank, world, local, with_c
         shape = [int(v) for v in args.launch.split(",")]
         for s in schemes:
             if s in ("picard", "full", "frozen"):
-                sims[s].set_launch(*shape)
-                tuned[s] = {"launch(threads,bps,chunk,ppt,lanes)": shape, "ms": None}
+                autotune.apply(sims[s], shape)
+                tuned[s] = {"launch(threads,bps,chunk,ppt,lanes[,tenor])": shape, "ms": None}
     elif tune:
-        cands = [(128, 0, 0, 1, 1), (256, 0, 0, 1, 1), (128, 0, 0, 1, 2), (256, 0, 0, 1, 2)]
+        # one lane per path (paths per thread 1 or 2), and the tenor-parallel mapping
+        cands = [(128, 0, 0, 1, 1), (256, 0, 0, 1, 1), (128, 0, 0, 1, 2), (256, 0, 0, 1, 2),
+                 (0, 0, 0, 0, 0, 8), (0, 0, 0, 0, 0, 16)]
         for s in schemes:
             if s in ("picard", "full", "frozen"):
                 r = autotune.tune(sims[s], s, candidates=cands, repeats=2, use_cache=False)
-                tuned[s] = {"launch(threads,bps,chunk,ppt,lanes)": r["launch"], "ms": r["ms"]}
+                tuned[s] = {"launch(threads,bps,chunk,ppt,lanes[,tenor])": r["launch"], "ms": r["ms"]}
 
     for _ in range(warmup):
         one_step()
@@ -556,12 +558,14 @@ def run_single(args, wl, schemes, steps, warmup, dev, rank, world, local, with_c
     def quad_roofline(s):
         ms = statistics.mean(per_scheme_ms[s])
         ach = units * 3 * wl.Q / (ms * 1e-3) / 1e12
-        shape = tuned.get(s, {}).get("launch(threads,bps,chunk,ppt,lanes)")
+        shape = tuned.get(s, {}).get("launch(threads,bps,chunk,ppt,lanes[,tenor])")
         lanes = shape[4] if shape and shape[4] else 1
-        traffic = _traffic(f"{s}/QP{wl.Q}/lanes{lanes}") if wl.paths == 1 << 20 else None
+        tenor = shape[5] if shape and len(shape) > 5 else 0
+        traffic = (_traffic(f"{s}/QP{wl.Q}/lanes{lanes}") if wl.paths == 1 << 20 and not tenor else None)
         r = {"bound": "alu", "achieved": ach, "peak": pk["fp32"], "unit": "TFP32-lane-op/s",
              "frac": ach / pk["fp32"], "frac_of_nominal_128_lanes": ach / pk["fp32_nominal"], "traffic": traffic,
-             "kernel": f"{s} path kernel, QP={wl.Q}", "peak_basis": pk["fp32_basis"]}
+             "kernel": (f"{s} tenor-parallel kernel ({tenor} lanes per path), QP={wl.Q}" if tenor
+                        else f"{s} path kernel, QP={wl.Q}"), "peak_basis": pk["fp32_basis"]}
         if clocks and clocks.get("sm_mhz"):
             r["frac_at_sampled_clock"] = r["frac"] * pk["sm_max_mhz"] / clocks["sm_mhz"]
         return r
@@ -613,7 +617,7 @@ def run_single(args, wl, schemes, steps, warmup, dev, rank, world, local, with_c
             for s in schemes:
                 sim = lll.LevyLibor(wl, x, W, stream=stream)
                 if s in tuned:
-                    sim.set_launch(*tuned[s]["launch(threads,bps,chunk,ppt,lanes)"])
+                    autotune.apply(sim, tuned[s]["launch(threads,bps,chunk,ppt,lanes[,tenor])"])
                 if s == "mlp":
                     lll.lll_mlp_init(sim.ctx, hid, lay, 0)
                     lll.lll_mlp_params(sim.ctx, 1, mlp_params[0], scales=mlp_params[1])
@@ -663,6 +667,47 @@ def run_single(args, wl, schemes, steps, warmup, dev, rank, world, local, with_c
     return line
 
 
+def run_mappings(args, rates=None):
+    """Path mapping against the tenor-parallel mapping: device time of one
+    simulation of the N=40 term structure (full and Picard) at 2^20 paths and
+    at 2^12 paths, for one lane per path (128 and 256 threads per block) and
+    for 4, 8, 16 and 32 lanes per path; each with its fraction of the FP32
+    roofline (3Q lane-ops per unit against the measured packed-FMA rate).
+    Returns the JSON line."""
+    import torch
+
+    from paper_1006_3340_gb300 import autotune, lll
+
+    dev = torch.device("cuda", 0)
+    pk = _alu_peaks(lll, torch, dev, rates)
+    shapes = [("path, 128 threads", (128, 0, 0, 1, 1)), ("path, 256 threads", (256, 0, 0, 1, 1)),
+              ("path, 2 paths/thread", (128, 0, 0, 2, 1))] + \
+             [(f"tenor, {g} lanes/path", (0, 0, 0, 0, 0, g)) for g in (4, 8, 16, 32)]
+    rows = []
+    for paths in (1 << 20, 1 << 12):
+        wl = workloads.large_single(paths=paths)
+        x, W = lll.lll_build_nig_quadrature(wl.alpha, wl.beta, wl.dbar, wl.a, wl.Q)
+        sim = lll.LevyLibor(wl, x, W)
+        try:
+            for scheme in ("picard", "full"):
+                for name, cand in shapes:
+                    autotune.apply(sim, cand)
+                    sim.simulate(scheme)  # warm-up
+                    ms = []
+                    for _ in range(max(3, args.steps)):
+                        sim.simulate(scheme)
+                        ms.append(sim.kernel_ms()[0])
+                    t = statistics.median(ms)
+                    ach = paths * wl.units_per_path() * 3 * wl.Q / (t * 1e-3) / 1e12
+                    rows.append({"paths": paths, "scheme": scheme, "mapping": name, "kernel_ms": t,
+                                 "units_per_s": paths * wl.units_per_path() / (t * 1e-3),
+                                 "fp32_frac": ach / pk["fp32"]})
+        finally:
+            sim.close()
+    return {"metric": "path-kernel device time per mapping", "workload": "large_single (N=40, Q=64)",
+            "fp32_peak_basis": pk["fp32_basis"], "rows": rows}
+
+
 def _extra_block(line):
     """The figures of another configuration kept in the headline line."""
     keep = ("value", "unit", "ms_per_step", "steps", "warmup", "config", "per_scheme", "caplets_per_s",
@@ -687,11 +732,13 @@ def main():
     ap.add_argument("--mlp-kernel", default="auto", choices=["auto", "warp", "tc"],
                     help="LLL_MLP kernel: tcgen05/TMEM (tc), mma.sync (warp) or the library's choice")
     ap.add_argument("--launch", default="", help="fixed launch shape for the quadrature schemes: "
-                    "threads,blocks_per_sm,chunk_rows,paths_per_thread,lanes_per_path (no tuning)")
-    ap.add_argument("--workload", default="large_single", choices=["large_single", "long_dated", "batch256"],
+                    "threads,blocks_per_sm,chunk_rows,paths_per_thread,lanes_per_path[,tenor_lanes] (no tuning)")
+    ap.add_argument("--workload", default="large_single",
+                    choices=["large_single", "long_dated", "batch256", "mappings"],
                     help="large_single: the N=40 term structure, 2^20 paths (default); long_dated: N=120, "
                     "Q=96, 2^22 paths; batch256: 256 uneven term structures in one launch per scheme "
-                    "(Picard and full only)")
+                    "(Picard and full only); mappings: path against tenor-parallel mapping, N=40, "
+                    "2^20 and 2^12 paths (a table, not a benchmark line)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -715,6 +762,9 @@ def main():
     from paper_1006_3340_gb300 import lll
 
     rates = lll.lll_measure_pipe_rates()
+    if args.workload == "mappings":
+        print(json.dumps(run_mappings(args, rates)), flush=True)
+        return 0
     if args.workload == "batch256":
         line = run_batch(args, args.steps, args.warmup, not args.no_cpu_baseline, not args.no_e2e, rates)
     else:

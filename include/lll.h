@@ -161,6 +161,26 @@ int lll_get_paths(lll_ctx *ctx, uint64_t first, uint64_t count, float *out);
 int lll_set_launch(lll_ctx *ctx, int threads_per_block, int blocks_per_sm, int chunk_rows,
                    int paths_per_thread, int lanes_per_path);
 
+/* lll_set_mapping -- how the full and Picard schemes map a path onto lanes.
+ *   LLL_MAP_PATH (0, default): one lane carries a path (or a lane group of
+ *     lll_set_launch shares the node sweep of as many paths) and sweeps its
+ *     live rates from the last one down, sharing the suffix products of the
+ *     beta factors between rates.
+ *   LLL_MAP_TENOR (1): tenor-parallel (Section 3.1-3.2: under the Picard
+ *     iterate of Eq. (Picard-2) every (path, tenor) evolves on its own):
+ *     `lanes` (4, 8, 16 or 32) lanes share a path, lane g owning the rate
+ *     block n - g r .. n - (g+1) r + 1, r = ceil(n / lanes) rounded up to odd.
+ *     Each lane multiplies the beta factors of its block per node, a
+ *     multiplicative scan over the lanes gives every lane the product over
+ *     the blocks above, and each lane sweeps and steps its own rates.  About
+ *     5/3 of the one-lane arithmetic plus the scan, for `lanes` times the
+ *     threads per path: for small path budgets.  128-thread blocks; caplet
+ *     payoffs and a node table only (LLL_EUNSUPPORTED otherwise at simulation).
+ * Other schemes ignore the mapping. */
+#define LLL_MAP_PATH 0
+#define LLL_MAP_TENOR 1
+int lll_set_mapping(lll_ctx *ctx, int mapping, int lanes);
+
 /* lll_kernel_ms -- device time of the last simulation's path kernel and of the
  * whole lll_simulate call, from CUDA events on the context's stream.
  * Synchronises the stream. */

@@ -3,9 +3,11 @@
 For a model context (or a batch) and a scheme it times candidate launch
 shapes -- threads per block, lanes per path (1: one lane sweeps all nodes of
 its path; 4: four lanes share the node sweep of four paths), table rows per
-staged chunk, resident blocks per SM -- with the library's own CUDA-event
-timing of the path kernel, keeps the fastest, and caches the choice per GPU,
-workload shape and scheme in ``_build/autotune.json`` (a per-machine file).
+staged chunk, resident blocks per SM, and the mapping (a sixth value G > 0
+selects the tenor-parallel kernel with G lanes per path, each owning a block
+of rates) -- with the library's own CUDA-event timing of the path kernel,
+keeps the fastest, and caches the choice per GPU, workload shape and scheme
+in ``_build/autotune.json`` (a per-machine file).
 """
 from __future__ import annotations
 
@@ -20,9 +22,17 @@ from . import lll
 CACHE = os.path.join(_build.BUILD, "autotune.json")
 
 DEFAULT_CANDIDATES = [
-    # (threads, blocks_per_sm, chunk_rows, paths_per_thread, lanes_per_path)
+    # (threads, blocks_per_sm, chunk_rows, paths_per_thread, lanes_per_path[, tenor lanes])
     (t, 0, c, 1, l) for t, c, l in itertools.product((64, 128, 256), (0, 16), (1, 4))
-]
+] + [(0, 0, 0, 0, 0, g) for g in (4, 8, 16, 32)]
+
+
+def apply(sim: "lll.LevyLibor", cand) -> None:
+    """Set a candidate: the five launch values, then the mapping (sixth value,
+    0 or absent: one lane per path; G: tenor-parallel with G lanes per path)."""
+    sim.set_launch(*cand[:5])
+    g = cand[5] if len(cand) > 5 else 0
+    sim.set_mapping("tenor" if g else "path", g)
 
 
 def _gpu_name() -> str:
@@ -65,12 +75,12 @@ def tune(sim: "lll.LevyLibor", scheme: str, paths: Optional[int] = None,
     if use_cache:
         hit = _load().get(key)
         if hit:
-            sim.set_launch(*hit["launch"])
+            apply(sim, hit["launch"])
             return dict(hit, cached=True)
     results = []
     for cand in candidates:
         try:
-            sim.set_launch(*cand)
+            apply(sim, cand)
             sim.simulate(scheme, paths=paths)  # warm-up
             best = min(_timed(sim, scheme, paths) for _ in range(repeats))
             results.append((best, cand))
@@ -80,7 +90,7 @@ def tune(sim: "lll.LevyLibor", scheme: str, paths: Optional[int] = None,
         raise RuntimeError("no launch shape ran")
     results.sort()
     ms, launch = results[0]
-    sim.set_launch(*launch)
+    apply(sim, launch)
     entry = {"launch": list(launch), "ms": ms, "tried": [[m, list(c)] for m, c in results]}
     _store(key, entry)
     return dict(entry, cached=False)

@@ -89,6 +89,7 @@ int record_error(lll_ctx *ctx, int code, const char *msg) { return fail(ctx, cod
 
 int launch_plan(const LaunchPlan &plan, const PathArgs &a)
 {
+    if (plan.tenor > 0) return launch_tenor_kernel(plan.scheme, plan.qp, plan.tenor, plan.grid, plan.smem, plan.stream, a);
     if (plan.lpp > 1)
         return launch_group_kernel(plan.scheme, plan.qp, plan.lpp, plan.grid, plan.threads, plan.smem, plan.stream, a);
     return launch_path_kernel(plan.scheme, plan.qp, plan.ppt, plan.grid, plan.threads, plan.smem, plan.stream, a);
@@ -97,7 +98,7 @@ int launch_plan(const LaunchPlan &plan, const PathArgs &a)
 // Same launch shape and arguments as lll_simulate, with no allocation: the
 // per-block scratch sizes are returned for the caller to place.
 int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, uint64_t seed,
-                LaunchPlan *plan)
+                LaunchPlan *plan, bool allow_tenor)
 {
     if (!ctx) return fail(nullptr, LLL_EINVAL, "ctx is NULL");
     if (!plan) return fail(ctx, LLL_EINVAL, "plan is NULL");
@@ -109,21 +110,34 @@ int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, u
     if (paths == 0) return fail(ctx, LLL_EINVAL, "paths must be > 0");
     if (first_path + paths < first_path) return fail(ctx, LLL_EINVAL, "path range overflows");
     const int QPk = (scheme == LLL_FROZEN) ? 0 : ctx->QP;
+    // Tenor-parallel mapping (lll_set_mapping): G lanes per path, full and
+    // Picard with a node table and caplet payoffs; other schemes keep the
+    // path mapping.
+    const int G = (allow_tenor && ctx->tenor_lanes > 0 && (scheme == LLL_FULL || scheme == LLL_PICARD))
+                      ? ctx->tenor_lanes : 0;
+    if (G > 0) {
+        if (QPk == 0 || ctx->product != LLL_PRODUCT_CAPLET || !tenor_kernel_supported(scheme, QPk, G))
+            return fail(ctx, LLL_EUNSUPPORTED, "the tenor-parallel mapping needs a node table and caplet payoffs");
+    }
     // Lanes per group of paths: 1 (one lane sweeps all nodes of its path) or
     // 2 / 4 (lane groups share the node sweep); the default is 1.
-    const int lpp = ctx->lpp > 0 ? ctx->lpp : 1;
-    const int R = lpp > 1 ? 1 : (ctx->ppt > 0 ? ctx->ppt : 1);
+    const int lpp = G > 0 ? 1 : (ctx->lpp > 0 ? ctx->lpp : 1);
+    const int R = (lpp > 1 || G > 0) ? 1 : (ctx->ppt > 0 ? ctx->ppt : 1);
     if (lpp > 1 && !group_kernel_supported(scheme, QPk, lpp))
         return fail(ctx, LLL_EUNSUPPORTED, "lane groups need a node table (NIG, full or Picard)");
-    if (lpp == 1 && !path_kernel_supported(scheme, QPk, R))
+    if (G == 0 && lpp == 1 && !path_kernel_supported(scheme, QPk, R))
         return fail(ctx, LLL_EUNSUPPORTED, "no kernel for this Q and paths per thread");
-    const int T = ctx->threads, CH = ctx->chunk_rows;
-    const size_t smem = lpp > 1 ? group_kernel_smem(QPk, ctx->n, ctx->ns, T, CH)
+    const int T = G > 0 ? tenor_kernel_threads() : ctx->threads, CH = ctx->chunk_rows;
+    const size_t smem = G > 0 ? tenor_kernel_smem(QPk, ctx->n, ctx->ns, G)
+                      : lpp > 1 ? group_kernel_smem(QPk, ctx->n, ctx->ns, T, CH)
                                 : path_kernel_smem(QPk, ctx->n, ctx->ns, T, CH);
     if (smem > 227 * 1024) return fail(ctx, LLL_EUNSUPPORTED, "shared memory need exceeds 227 KB");
     int occ = 0;
     cudaError_t e;
-    if (lpp > 1) {
+    if (G > 0) {
+        e = (cudaError_t)tenor_kernel_prepare(scheme, QPk, G, smem, &occ);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "tenor kernel attributes");
+    } else if (lpp > 1) {
         e = (cudaError_t)group_kernel_prepare(scheme, QPk, lpp, smem, T, &occ);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "group kernel attributes");
     } else {
@@ -134,7 +148,8 @@ int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, u
     }
     if (occ < 1) return fail(ctx, LLL_EUNSUPPORTED, "launch shape does not fit on an SM");
     const int bps = ctx->blocks_per_sm > 0 ? std::min(ctx->blocks_per_sm, occ) : occ;
-    const uint64_t tiles = (paths + (uint64_t)T * R - 1) / ((uint64_t)T * R);
+    const uint64_t per_tile = G > 0 ? (uint64_t)(T / G) : (uint64_t)T * R; // paths per block tile
+    const uint64_t tiles = (paths + per_tile - 1) / per_tile;
     const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)bps * ctx->sm_count);
     const int nst = (scheme == LLL_PICARD) ? 2 : 1;
     PathArgs a{};
@@ -157,8 +172,10 @@ int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, u
     }
     plan->args = a;
     plan->scheme = scheme; plan->qp = QPk; plan->ppt = R; plan->lpp = lpp; plan->threads = T; plan->grid = grid;
+    plan->tenor = G;
     plan->smem = smem;
-    plan->state_floats_per_block = (size_t)R * nst * ctx->n * T;
+    // the tenor-parallel kernel keeps its path state in shared memory
+    plan->state_floats_per_block = G > 0 ? 0 : (size_t)R * nst * ctx->n * T;
     plan->partial_doubles_per_block = (size_t)ctx->n * ctx->ns * 2;
     plan->n_out = ctx->n * ctx->ns * 2;
     plan->stream = ctx->stream;
@@ -361,6 +378,20 @@ int lll_set_launch(lll_ctx *ctx, int threads_per_block, int blocks_per_sm, int c
     if (threads_per_block) ctx->threads = threads_per_block;
     ctx->blocks_per_sm = blocks_per_sm;
     ctx->chunk_rows = chunk_rows ? std::min(chunk_rows, ctx->n) : default_chunk_rows(ctx->n, ctx->QP);
+    return LLL_OK;
+}
+
+int lll_set_mapping(lll_ctx *ctx, int mapping, int lanes)
+{
+    if (!ctx) return fail(nullptr, LLL_EINVAL, "ctx is NULL");
+    if (mapping == LLL_MAP_PATH) {
+        ctx->tenor_lanes = 0;
+        return LLL_OK;
+    }
+    if (mapping != LLL_MAP_TENOR) return fail(ctx, LLL_EINVAL, "unknown mapping");
+    if (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
+        return fail(ctx, LLL_EINVAL, "lanes must be 4, 8, 16 or 32");
+    ctx->tenor_lanes = lanes;
     return LLL_OK;
 }
 

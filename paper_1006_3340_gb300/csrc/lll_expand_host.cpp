@@ -90,7 +90,7 @@ int simulate_expand(lll_ctx *ctx, int order, uint64_t first_path, uint64_t paths
     if ((order == 2 && ctx->n > 16) || ctx->n > 64)
         return record_error(ctx, LLL_EUNSUPPORTED, "drift expansions: n <= 16 rates (second order), n <= 64 (first)");
     LaunchPlan plan;
-    int rc = plan_launch(ctx, LLL_FULL, first_path, paths, seed, &plan);
+    int rc = plan_launch(ctx, LLL_FULL, first_path, paths, seed, &plan, false);
     if (rc != LLL_OK) return rc;
     if (ctx->expand_order != order) {
         rc = build_tables(ctx, order);

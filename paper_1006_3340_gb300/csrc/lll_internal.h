@@ -57,6 +57,7 @@ struct BatchArgs {
 struct LaunchPlan {
     PathArgs args;
     int scheme, qp, ppt, lpp, threads, grid; // lpp: lanes per group of paths (1, 2 or 4)
+    int tenor;                               // > 0: tenor-parallel kernel with this many lanes per path
     size_t smem;
     size_t state_floats_per_block, partial_doubles_per_block;
     int n_out; // doubles written by the final reduction: n * n_strikes * 2
@@ -79,6 +80,13 @@ size_t group_kernel_smem(int QP, int n, int ns, int threads, int chunk_rows);
 int group_kernel_prepare(int scheme, int QP, int G, size_t smem, int threads, int *blocks_per_sm);
 int launch_group_kernel(int scheme, int QP, int G, int grid, int threads, size_t smem, cudaStream_t st,
                         const PathArgs &a);
+// Launchers implemented in lll_paths_tenor.cu (G lanes per path, each owning a block of rates).
+int tenor_rates_per_lane(int n, int G);
+bool tenor_kernel_supported(int scheme, int QP, int G);
+size_t tenor_kernel_smem(int QP, int n, int ns, int G);
+int tenor_kernel_threads();
+int tenor_kernel_prepare(int scheme, int QP, int G, size_t smem, int *blocks_per_sm);
+int launch_tenor_kernel(int scheme, int QP, int G, int grid, size_t smem, cudaStream_t st, const PathArgs &a);
 struct LaunchPlan;
 int launch_plan(const LaunchPlan &plan, const PathArgs &a);
 bool batch_kernel_supported(int scheme, int QP);
@@ -99,7 +107,9 @@ int launch_finalize(const double *partials, int grid, int n_out, double *sums, c
 struct lll_ctx;
 namespace lll {
 // Implemented in lll_capi.cpp.
+// allow_tenor: honour the context's tenor-parallel mapping (lll_set_mapping);
+// callers that only need the path arguments of the full scheme pass false.
 int plan_launch(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, uint64_t seed,
-                LaunchPlan *plan);
+                LaunchPlan *plan, bool allow_tenor = true);
 int record_error(lll_ctx *ctx, int code, const char *msg);
 }  // namespace lll

@@ -454,7 +454,7 @@ int lll_mlp_train(lll_ctx *ctx, const lll_mlp_cfg *cfg, double *final_loss)
     const uint64_t P = cfg->train_paths, nrec = P * R;
     // 1. training data from the quadrature full scheme
     LaunchPlan plan;
-    rc = plan_launch(ctx, LLL_FULL, 0, P, cfg->seed ^ 0x5EED5EEDull, &plan);
+    rc = plan_launch(ctx, LLL_FULL, 0, P, cfg->seed ^ 0x5EED5EEDull, &plan, false);
     if (rc != LLL_OK) return rc;
     float *state = nullptr, *rec_u = nullptr, *rec_y = nullptr;
     int *rec_k = nullptr;
@@ -537,7 +537,7 @@ namespace lll {
 int simulate_mlp_layered(lll_ctx *ctx, MlpState *m, uint64_t first_path, uint64_t paths, uint64_t seed)
 {
     LaunchPlan plan;
-    int rc = plan_launch(ctx, LLL_FULL, first_path, paths, seed, &plan);
+    int rc = plan_launch(ctx, LLL_FULL, first_path, paths, seed, &plan, false);
     if (rc != LLL_OK) return rc;
     const int n = ctx->n, s = ctx->s, S = ctx->S, ns = ctx->ns;
     const int T = mlp_layered_threads();
@@ -643,7 +643,7 @@ int simulate_mlp(lll_ctx *ctx, uint64_t first_path, uint64_t paths, uint64_t see
         use_tc = tc_ok;
     }
     LaunchPlan plan;
-    int rc = plan_launch(ctx, LLL_FULL, first_path, paths, seed, &plan);
+    int rc = plan_launch(ctx, LLL_FULL, first_path, paths, seed, &plan, false);
     if (rc != LLL_OK) return rc;
     const size_t smem = use_tc ? smem_tc : mlp_path_smem(m->layers, m->in_pad, ctx->n, ctx->ns);
     int occ = 0;

@@ -10,7 +10,8 @@
 // independent dependency chains of one instruction, and times the block with
 // the SM's cycle counter.  Results per SM per clock:
 //   [0] tanh.approx.f32 (one per SiLU of the learned compensator),
-//   [1] ex2.approx.ftz.f32, [2] rcp.approx.ftz.f32 (the weight w of a rate),
+//   [1] ex2.approx.ftz.f32, [2] rcp.approx.ftz.f32 (the weight w of a rate;
+//       each followed by an FP32 add, which keeps the chain from folding),
 //   [3] FP32 lane-ops of packed fma.rn.f32x2 (two per lane and instruction:
 //       the sweep of the quadrature compensator issues these),
 //   [4] FP32 lane-ops of scalar fma.rn.f32.
@@ -60,7 +61,9 @@ __global__ void __launch_bounds__(kProbeThreads) pipe_kernel(float seed, unsigne
         for (int c = 0; c < kChains; ++c) {
             if (OP == TANH) asm volatile("tanh.approx.f32 %0, %0;" : "+f"(v[c]));
             if (OP == EX2) asm volatile("ex2.approx.ftz.f32 %0, %0;" : "+f"(v[c]));
-            if (OP == RCP) asm volatile("rcp.approx.ftz.f32 %0, %0;" : "+f"(v[c]));
+            // rcp(rcp(x)) could be folded by the assembler: an add between keeps
+            // the chain (it issues to the FMA pipe, not the MUFU).
+            if (OP == RCP) asm volatile("rcp.approx.ftz.f32 %0, %0;\n\tadd.f32 %0, %0, 0f3F800000;" : "+f"(v[c]));
             if (OP == FFMA) asm volatile("fma.rn.f32 %0, %0, 0f3F7FBE77, 0f3A83126F;" : "+f"(v[c]));
             if (OP == FFMA2) v2[c] = __ffma2_rn(v2[c], a2, b2);
         }

@@ -79,6 +79,7 @@ def load():
         "lll_price_caplets": (I, [V, _dp, _dp]),
         "lll_get_paths": (I, [V, U64, U64, _fp]),
         "lll_set_launch": (I, [V, I, I, I, I, I]),
+        "lll_set_mapping": (I, [V, I, I]),
         "lll_kernel_ms": (I, [V, _fp, _fp]),
         "lll_build_nig_quadrature": (I, [lll_nig, ctypes.c_double, I, _dp, _dp]),
         "lll_mlp_init": (I, [V, I, I, U64]),
@@ -203,6 +204,15 @@ def lll_get_paths(ctx, n, first, count):
 def lll_set_launch(ctx, threads=0, blocks_per_sm=0, chunk_rows=0, paths_per_thread=0, lanes_per_path=0):
     _check(load().lll_set_launch(ctx, int(threads), int(blocks_per_sm), int(chunk_rows),
                                  int(paths_per_thread), int(lanes_per_path)), ctx)
+
+
+LLL_MAP_PATH, LLL_MAP_TENOR = 0, 1
+
+
+def lll_set_mapping(ctx, mapping, lanes=0):
+    """mapping: "path" (one lane per path) or "tenor" (``lanes`` lanes per path)."""
+    m = {"path": LLL_MAP_PATH, "tenor": LLL_MAP_TENOR}.get(mapping, mapping)
+    _check(load().lll_set_mapping(ctx, int(m), int(lanes)), ctx)
 
 
 def lll_kernel_ms(ctx):
@@ -435,6 +445,9 @@ class LevyLibor:
 
     def set_launch(self, threads=0, blocks_per_sm=0, chunk_rows=0, paths_per_thread=0, lanes_per_path=0):
         lll_set_launch(self.ctx, threads, blocks_per_sm, chunk_rows, paths_per_thread, lanes_per_path)
+
+    def set_mapping(self, mapping, lanes=0):
+        lll_set_mapping(self.ctx, mapping, lanes)
 
     def close(self):
         if self.ctx:

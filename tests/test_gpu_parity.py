@@ -33,13 +33,15 @@ def lll():
     return mod
 
 
-def _compare(lll, wl, scheme, npaths, launch=None, x=None, W=None):
+def _compare(lll, wl, scheme, npaths, launch=None, x=None, W=None, tenor=0):
     if x is None:
         x, W = quadrature.rule_for(wl)
     sim = lll.LevyLibor(wl, x, W)
     try:
         if launch:
             sim.set_launch(*launch)
+        if tenor:
+            sim.set_mapping("tenor", tenor)
         sim.simulate(scheme, paths=npaths, snapshots=npaths)
         zg = sim.paths(0, npaths).astype(np.float64)
         pg, seg = sim.prices()
@@ -95,3 +97,51 @@ def test_tiny_edge_shapes(lll, N, s, Q, paths, scheme, lanes):
 def test_launch_shapes_agree(lll, launch):
     wl = workloads.large_single()
     _compare(lll, wl, "picard", 300, launch=launch)
+
+
+# Tenor-parallel mapping (lll_set_mapping): G lanes per path, each owning a
+# block of rates; shapes where the last lanes own fewer rates or none (n=39,
+# G=16 gives r=3 and 13 busy lanes; n=9, G=32), ragged path tiles, one path.
+@pytest.mark.parametrize("lanes", [4, 8, 16, 32])
+@pytest.mark.parametrize("scheme", ["full", "picard"])
+def test_tenor_mapping_large_single(lll, scheme, lanes):
+    wl = workloads.large_single()
+    _compare(lll, wl, scheme, 1000 + 37, tenor=lanes)
+
+
+@pytest.mark.parametrize("lanes", [4, 32])
+@pytest.mark.parametrize("scheme", ["full", "picard"])
+def test_tenor_mapping_small_plain(lll, scheme, lanes):
+    wl = workloads.small_plain(paths=3001)
+    _compare(lll, wl, scheme, 3001, tenor=lanes)
+
+
+@pytest.mark.parametrize("N,s,Q,paths", [(2, 1, 8, 1), (3, 2, 8, 33), (7, 4, 40, 129)])
+@pytest.mark.parametrize("lanes", [4, 8])
+def test_tenor_mapping_tiny_edge_shapes(lll, N, s, Q, paths, lanes):
+    wl = workloads.tiny(N=N, s=s, Q=Q, paths=paths)
+    for scheme in ("full", "picard"):
+        _compare(lll, wl, scheme, paths, tenor=lanes)
+
+
+@pytest.mark.parametrize("scheme", ["full", "picard"])
+def test_tenor_mapping_long_dated(lll, scheme):
+    wl = workloads.long_dated()
+    _compare(lll, wl, scheme, 100, tenor=8)
+
+
+def test_tenor_mapping_refuses_swaptions_and_keeps_other_schemes(lll):
+    wl = workloads.small_plain(paths=500)
+    x, W = quadrature.rule_for(wl)
+    sim = lll.LevyLibor(wl, x, W)
+    try:
+        sim.set_mapping("tenor", 8)
+        sim.simulate("frozen")  # frozen drift keeps the path kernel
+        sim.set_product("swaption")
+        with pytest.raises(lll.LLLError) as e:
+            sim.simulate("picard")
+        assert e.value.code == lll.LLL_EUNSUPPORTED
+        sim.set_mapping("path")
+        sim.simulate("picard")
+    finally:
+        sim.close()
