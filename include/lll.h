@@ -364,6 +364,38 @@ int lll_mlp_eval(lll_ctx *ctx, const float *x, const float *y, int rows, float *
 #define LLL_MLP_KERNEL_LAYERED 3
 int lll_mlp_set_kernel(lll_ctx *ctx, int kind);
 
+/* lll_set_gemm_kernel -- the tensor-core kernel of the learned compensator's
+ * GEMMs (training: forward, dX and split-K dW; LLL_MLP_KERNEL_LAYERED
+ * inference), for the whole process:
+ *   LLL_GEMM_TC (0, default): tcgen05.mma, operands in shared memory
+ *     (128-byte swizzle), FP32 accumulator in tensor memory, 128 x N tiles
+ *     (N = 64, 128 or 256), bounded waits (a wait that gives up makes
+ *     lll_mlp_train return LLL_ETIMEOUT);
+ *   LLL_GEMM_MMA_SYNC (1): the warp-level mma.sync.m16n8k16 kernel.
+ * Both compute the same products with FP32 accumulation (in different
+ * orders).  Not thread-safe against concurrent training in other threads. */
+#define LLL_GEMM_TC 0
+#define LLL_GEMM_MMA_SYNC 1
+int lll_set_gemm_kernel(int kind);
+
+/* lll_gemm_bf16 -- one product of the kernel lll_set_gemm_kernel selected,
+ * on host buffers (for tests of the GEMM itself; allocates and frees device
+ * memory and synchronises the device).  BF16 operands as raw bits:
+ *   C[m][n] = sum_k A(m,k) B(k,n), A(m,k) = A[m*lda+k] (ta = 0) or
+ *   A[k*lda+m] (ta = 1), B(k,n) = B[k*ldb+n] (tb = 0) or B[n*ldb+k] (tb = 1).
+ *   epi 0: C = the product (split-K over `splits` ranges, added in order);
+ *   epi 1 (ta = 0, tb = 1, the forward layer): C = z = product + bias[n],
+ *          H = bf16(SiLU(z)), SiLU(z) = z (1 + tanh(z/2)) / 2;
+ *   epi 2 (ta = 0, tb = 0, the backward layer): C = d = product *
+ *          SiLU'(Zin[m][n]), H = bf16(d);
+ *   epi 3 / 4 (ta = 0, tb = 1, tcgen05 only): C = product + bias[n] /
+ *          product + bias[m] (the vector head's output layer, computed
+ *          transposed in the layered inference).
+ * C, Zin: [M][N] FP32; H: [M][N] BF16 bits; bias: [N] ([M] for epi 4).  The paper has no
+ * counterpart: the GEMMs serve the learned compensator. */
+int lll_gemm_bf16(int ta, int tb, int epi, const uint16_t *A, int lda, const uint16_t *B, int ldb, int M, int N,
+                  int K, int splits, const float *bias, const float *Zin, float *C, uint16_t *H);
+
 /* lll_inject -- failure-detection testing: LLL_INJECT_MMA_STALL makes the
  * next launch of the tensor-memory MLP kernel issue no MMAs, so that its
  * bounded waits run out (about 2 s): the launch ends by itself, frees its

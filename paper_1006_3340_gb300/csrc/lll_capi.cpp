@@ -451,6 +451,7 @@ int lll_simulate(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, 
     CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], ctx->stream));
     ctx->simulated = true;
     ctx->err_pending = false;
+    ctx->gemm_err_pending = false;
     ctx->last_paths = paths;
     ctx->last_snap_paths = a.n_snap;
     return LLL_OK;
@@ -466,6 +467,16 @@ int lll_get_sums(lll_ctx *ctx, double *sum, double *sumsq, uint64_t *count)
     CUDA_TRY(ctx, cudaMemcpyAsync(buf.data(), ctx->d_sums, sizeof(double) * 2 * cnt,
                                   cudaMemcpyDeviceToHost, ctx->stream));
     CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->gemm_err_pending) {
+        int word = 0;
+        const cudaError_t e = (cudaError_t)mlp_gemm_take_error(&word, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "GEMM error word");
+        ctx->gemm_err_pending = false;
+        if (word != 0) {
+            ctx->simulated = false;
+            return fail(ctx, LLL_ETIMEOUT, "a bounded wait of the tensor-core GEMM gave up; results discarded");
+        }
+    }
     if (ctx->err_pending && ctx->d_err) {
         int word = 0;
         CUDA_TRY(ctx, cudaMemcpy(&word, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));

@@ -49,5 +49,6 @@ struct lll_ctx {
     int *d_err = nullptr;   // error word of kernels with bounded waits
     int inject = 0;         // LLL_INJECT_* for the next launch (failure-detection tests)
     bool err_pending = false;
+    bool gemm_err_pending = false; // the last simulation ran the layered GEMMs (their error word)
     std::string err;
 };

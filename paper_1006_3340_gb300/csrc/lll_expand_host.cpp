@@ -149,6 +149,7 @@ int simulate_expand(lll_ctx *ctx, int order, uint64_t first_path, uint64_t paths
 #undef XTRY
     ctx->simulated = true;
     ctx->err_pending = false;
+    ctx->gemm_err_pending = false;
     ctx->last_paths = paths;
     ctx->last_snap_paths = a.n_snap;
     return LLL_OK;

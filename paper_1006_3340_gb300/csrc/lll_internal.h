@@ -102,6 +102,11 @@ int launch_frozen_drift(const double *lam, const double *x, const double *W, con
                         cudaStream_t st);
 int launch_finalize(const double *partials, int grid, int n_out, double *sums, cudaStream_t st);
 
+// Implemented in lll_gemm_tc.cu: read and clear the error word of the tcgen05
+// GEMMs on the current device (non-zero: a bounded wait gave up since the
+// last read).  Synchronises the stream.
+int mlp_gemm_take_error(int *word, cudaStream_t st);
+
 }  // namespace lll
 
 struct lll_ctx;

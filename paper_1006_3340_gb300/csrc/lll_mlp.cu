@@ -62,7 +62,7 @@ __device__ __forceinline__ float silu_grad(float z)
 //   A(m, k) = A[m * lda + k]  (TA = 0)   or  A[k * lda + m]  (TA = 1)
 //   B(k, n) = B[k * ldb + n]  (TB = 0)   or  B[n * ldb + k]  (TB = 1)
 // EPI 0: write FP32 C (+ z * M * N for split-K partials).
-// EPI 1: z = C + bias[n]; Zout = z (FP32); Hout = bf16(SiLU(z)).
+// EPI 1: z = C + bias[n]; Zout = z (FP32, if given); Hout = bf16(SiLU(z)).
 // EPI 2: Hout = bf16(C * SiLU'(Zin[m, n])); Zout = that value in FP32.
 template <int TA, int TB, int EPI>
 __global__ void __launch_bounds__(128) gemm_bf16(const __nv_bfloat16 *__restrict__ A, int lda,
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(128) gemm_bf16(const __nv_bfloat16 *__restrict
                     C[(size_t)blockIdx.z * M * N + o] = v;
                 } else if (EPI == 1) {
                     const float z = v + bias[gn];
-                    Zout[o] = z;
+                    if (Zout) Zout[o] = z;
                     Hout[o] = __float2bfloat16(silu(z));
                 } else {
                     const float d = v * silu_grad(Zin[o]);
@@ -191,27 +191,26 @@ __global__ void out_loss(const __nv_bfloat16 *H, int Hdim, const __nv_bfloat16 *
 // targets y (rows x O) and the rows' Euler steps kr, the masked residual
 // over the live rates (o + 1 >= kr / s + 1, o < n): dout = 2 (out - y) / (rows n)
 // (FP32 and BF16), per-block sums of squares and live counts.  One thread per
-// row.
+// element (consecutive threads, consecutive outputs of a row: coalesced);
+// blocks of 128 elements, so the per-block partials are in a fixed order.
 __global__ void vec_loss(float *out, const float *b, const float *y, const int *kr, int rows, int O, int n, int s,
                          float *dout, __nv_bfloat16 *douth, double *loss_part, double *cnt_part)
 {
     __shared__ double red[2][128];
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     double l = 0.0, c = 0.0;
-    if (r < rows) {
-        const int imin = y ? kr[r] / s + 1 : 1;
-        const float inv = 2.0f / ((float)rows * (float)n);
-        for (int o = 0; o < O; ++o) {
-            const size_t e = (size_t)r * O + o;
-            const float v = out[e] + b[o];
-            out[e] = v;
-            if (!y) continue;
+    if (e < (size_t)rows * O) {
+        const int r = (int)(e / O), o = (int)(e % O);
+        const float v = out[e] + b[o];
+        out[e] = v;
+        if (y) {
+            const int imin = kr[r] / s + 1;
             float d = 0.0f;
             if (o < n && o + 1 >= imin) {
                 const float rr = v - y[e];
-                d = inv * rr;
-                l += (double)rr * rr;
-                c += 1.0;
+                d = 2.0f / ((float)rows * (float)n) * rr;
+                l = (double)rr * rr;
+                c = 1.0;
             }
             dout[e] = d;
             douth[e] = __float2bfloat16(d);
@@ -220,10 +219,10 @@ __global__ void vec_loss(float *out, const float *b, const float *y, const int *
     red[0][threadIdx.x] = l;
     red[1][threadIdx.x] = c;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            red[0][threadIdx.x] += red[0][threadIdx.x + o];
-            red[1][threadIdx.x] += red[1][threadIdx.x + o];
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + k];
+            red[1][threadIdx.x] += red[1][threadIdx.x + k];
         }
         __syncthreads();
     }
@@ -322,9 +321,9 @@ unsigned blocks_for(size_t count, int threads) { return (unsigned)((count + thre
 // ---------------------------------------------------------------------------
 // Host-side launch helpers (used by lll_mlp_host.cpp).
 // ---------------------------------------------------------------------------
-int mlp_gemm(int ta, int tb, int epi, const void *A, int lda, const void *B, int ldb, int M, int N,
-             int K, int splits, float *C, const float *bias, const float *Zin, float *Zout, void *Hout,
-             cudaStream_t st)
+int mlp_gemm_mma(int ta, int tb, int epi, const void *A, int lda, const void *B, int ldb, int M, int N,
+                 int K, int splits, float *C, const float *bias, const float *Zin, float *Zout, void *Hout,
+                 cudaStream_t st)
 {
     if (splits < 1) splits = 1;
     int k_chunk = (K + splits - 1) / splits;
@@ -347,7 +346,7 @@ int mlp_gemm(int ta, int tb, int epi, const void *A, int lda, const void *B, int
     return (int)cudaGetLastError();
 }
 
-int mlp_splits_used(int K, int splits)
+int mlp_splits_used_mma(int K, int splits)
 {
     if (splits < 1) splits = 1;
     int k_chunk = (K + splits - 1) / splits;
@@ -367,8 +366,9 @@ int mlp_out_loss(const void *H, int Hdim, const void *w, const float *b, const f
 int mlp_vec_loss(float *out, const float *b, const float *y, const int *kr, int rows, int O, int n, int s,
                  float *dout, void *douth, double *loss_part, double *cnt_part, cudaStream_t st)
 {
-    vec_loss<<<(rows + 127) / 128, 128, 0, st>>>(out, b, y, kr, rows, O, n, s, dout,
-                                                 static_cast<__nv_bfloat16 *>(douth), loss_part, cnt_part);
+    const size_t count = (size_t)rows * O;
+    vec_loss<<<blocks_for(count, 128), 128, 0, st>>>(out, b, y, kr, rows, O, n, s, dout,
+                                                     static_cast<__nv_bfloat16 *>(douth), loss_part, cnt_part);
     return (int)cudaGetLastError();
 }
 

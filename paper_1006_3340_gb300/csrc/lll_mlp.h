@@ -11,11 +11,23 @@
 
 namespace lll {
 
-// Split-K aware BF16 GEMM (see lll_mlp.cu for the operand conventions).
+// Split-K aware BF16 GEMM (see lll_mlp.cu for the operand conventions): the
+// tcgen05 kernel (lll_gemm_tc.cu, the default) or the mma.sync kernel
+// (lll_mlp.cu), chosen process-wide by lll_set_gemm_kernel.
 int mlp_gemm(int ta, int tb, int epi, const void *A, int lda, const void *B, int ldb, int M, int N,
              int K, int splits, float *C, const float *bias, const float *Zin, float *Zout, void *Hout,
              cudaStream_t st);
 int mlp_splits_used(int K, int splits);
+int mlp_gemm_kind(); // LLL_GEMM_TC or LLL_GEMM_MMA_SYNC (epilogue 3, C + bias, is tcgen05 only)
+int mlp_gemm_mma(int ta, int tb, int epi, const void *A, int lda, const void *B, int ldb, int M, int N,
+                 int K, int splits, float *C, const float *bias, const float *Zin, float *Zout, void *Hout,
+                 cudaStream_t st);
+int mlp_splits_used_mma(int K, int splits);
+int mlp_gemm_tc(int ta, int tb, int epi, const void *A, int lda, const void *B, int ldb, int M, int N, int K,
+                int splits, float *C, const float *bias, const float *Zin, float *Zout, void *Hout, int *err,
+                cudaStream_t st);
+int mlp_splits_used_tc(int K, int splits);
+
 int mlp_out_loss(const void *H, int Hdim, const void *w, const float *b, const float *y, int rows,
                  float *out, float *dout, double *loss_part, cudaStream_t st);
 int mlp_vec_loss(float *out, const float *b, const float *y, const int *kr, int rows, int O, int n, int s,
@@ -63,8 +75,9 @@ int launch_mlp_path(int layers, int in_pad, int grid, size_t smem, cudaStream_t 
 int mlp_layered_threads();
 int launch_mlp_features(const PathArgs &a, const MlpScales &sc, int k, int Pc, const float *state, void *X,
                         int in_pad, int head, cudaStream_t st);
+// out_t: the vector head's outputs are [outputs][Pc] (rates as rows), else [Pc][outputs]
 int launch_mlp_euler(const PathArgs &a, const float *Ctab, float y_scale, int k, uint64_t chunk_first, int Pc,
-                     float *state, const float *out, int outputs, double *acc, cudaStream_t st);
+                     float *state, const float *out, int outputs, int out_t, double *acc, cudaStream_t st);
 int launch_mlp_acc_to_partials(const double *acc, size_t cells, double *partials, cudaStream_t st);
 
 // lll_mlp_tc.cu (tcgen05, accumulators in tensor memory; hidden = 128)

@@ -140,7 +140,7 @@ int ensure_rows(lll_ctx *ctx, MlpState *m, int rows)
     if (ok && m->head)
         ok = cudaMalloc(&m->d_douth, 2 * (size_t)rows * O) == cudaSuccess &&
              cudaMalloc((void **)&m->d_kr, 4 * (size_t)rows) == cudaSuccess &&
-             cudaMalloc((void **)&m->d_cnt, sizeof(double) * ((rows + 127) / 128)) == cudaSuccess;
+             cudaMalloc((void **)&m->d_cnt, sizeof(double) * (((size_t)rows * O + 127) / 128)) == cudaSuccess;
     for (int l = 0; ok && l < m->layers; ++l) {
         void *hp = nullptr;
         float *zp = nullptr;
@@ -152,7 +152,8 @@ int ensure_rows(lll_ctx *ctx, MlpState *m, int rows)
     for (int i = 0; ok && i < 2; ++i)
         ok = cudaMalloc((void **)&m->d_dZ[i], 4 * (size_t)rows * H) == cudaSuccess &&
              cudaMalloc(&m->d_dZh[i], 2 * (size_t)rows * H) == cudaSuccess;
-    const int lb = (rows + 7) / 8;
+    // loss partials: one per 8 rows (per-rate head), one per 128 outputs (vector head)
+    const size_t lb = m->head ? ((size_t)rows * O + 127) / 128 : ((size_t)rows + 7) / 8;
     ok = ok && cudaMalloc((void **)&m->d_loss, sizeof(double) * lb) == cudaSuccess;
     if (!ok) {
         mlp_free_buffers(m);
@@ -183,12 +184,20 @@ int forward(lll_ctx *ctx, MlpState *m, int rows, const float *y)
     const void *Hin = m->d_X;
     int din = m->in_pad;
     for (int l = 0; l < m->layers; ++l) {
+        // pre-activations are kept only for a backward pass (training: y given)
         MTRY(mlp_gemm(0, 1, 1, Hin, din, ph + 2 * m->offW[l], din, rows, m->hidden, din, 1, nullptr,
-                      m->d_p + m->offb[l], nullptr, m->d_Z[l], m->d_H[l], st));
+                      m->d_p + m->offb[l], nullptr, y ? m->d_Z[l] : nullptr, m->d_H[l], st));
         Hin = m->d_H[l];
         din = m->hidden;
     }
     if (m->head) {
+        if (!y && mlp_gemm_kind() == LLL_GEMM_TC) {
+            // inference: out^T = W_out H^T + b_out (rates as rows, [outputs][rows]),
+            // the layout of the Euler kernel's path state
+            MTRY(mlp_gemm(0, 1, 4, ph + 2 * m->off_wout, m->hidden, Hin, m->hidden, m->outputs, rows, m->hidden, 1,
+                          m->d_out, m->d_p + m->off_bout, nullptr, nullptr, nullptr, st));
+            return LLL_OK;
+        }
         // out = H W_out^T (FP32), then bias and, with targets, the masked loss
         MTRY(mlp_gemm(0, 1, 0, Hin, m->hidden, ph + 2 * m->off_wout, m->hidden, rows, m->outputs, m->hidden, 1,
                       m->d_out, nullptr, nullptr, nullptr, nullptr, st));
@@ -249,8 +258,8 @@ int backward(lll_ctx *ctx, MlpState *m, int rows)
 double read_loss(lll_ctx *ctx, MlpState *m, int rows, bool *ok)
 {
     if (m->head) {
-        // mean over the live targets of the batch
-        const int lb = (rows + 127) / 128;
+        // mean over the live targets of the batch (one partial per 128 outputs)
+        const size_t lb = ((size_t)rows * m->outputs + 127) / 128;
         std::vector<double> part(lb), cnt(lb);
         *ok = cudaMemcpyAsync(part.data(), m->d_loss, sizeof(double) * lb, cudaMemcpyDeviceToHost, ctx->stream) ==
                   cudaSuccess &&
@@ -522,6 +531,10 @@ int lll_mlp_train(lll_ctx *ctx, const lll_mlp_cfg *cfg, double *final_loss)
     e = cudaStreamSynchronize(st);
     cleanup();
     if (e != cudaSuccess) return cerr(ctx, e, "training");
+    int word = 0;
+    e = (cudaError_t)mlp_gemm_take_error(&word, st);
+    if (e != cudaSuccess) return cerr(ctx, e, "GEMM error word");
+    if (word) return err(ctx, LLL_ETIMEOUT, "a bounded wait of the tensor-core GEMM gave up; training discarded");
     m->trained = true;
     if (final_loss) *final_loss = last;
     return LLL_OK;
@@ -542,7 +555,9 @@ int simulate_mlp_layered(lll_ctx *ctx, MlpState *m, uint64_t first_path, uint64_
     const int n = ctx->n, s = ctx->s, S = ctx->S, ns = ctx->ns;
     const int T = mlp_layered_threads();
     // chunk of paths: at most 2^20 rows per step (one per path and live rate,
-    // or one per path for the vector head), a multiple of the block size
+    // or one per path for the vector head), a multiple of the block size.
+    // (Chunks small enough for a layer's activations to stay in L2 measured
+    // slower: the products then have too few row tiles per SM.)
     const uint64_t rows_cap = 1u << 20;
     const uint64_t rows_per_path = m->head ? 1 : (uint64_t)n;
     uint64_t Pc = std::max<uint64_t>(T, (rows_cap / rows_per_path) / T * T);
@@ -595,7 +610,8 @@ int simulate_mlp_layered(lll_ctx *ctx, MlpState *m, uint64_t first_path, uint64_
             rc = forward(ctx, m, (int)(Pc * (m->head ? 1 : live)), nullptr);
             if (rc != LLL_OK) return rc;
             MTRY(launch_mlp_euler(a, ctx->d_C, m->sc.y_scale, k, c0, (int)Pc, ctx->d_state, m->d_out,
-                                  m->head ? m->outputs : 0, m->d_acc, st));
+                                  m->head ? m->outputs : 0, m->head && mlp_gemm_kind() == LLL_GEMM_TC, m->d_acc,
+                                  st));
         }
     }
     MTRY(cudaEventRecord(ctx->ev[1], st));
@@ -604,6 +620,7 @@ int simulate_mlp_layered(lll_ctx *ctx, MlpState *m, uint64_t first_path, uint64_
     MTRY(cudaEventRecord(ctx->ev[2], st));
     ctx->simulated = true;
     ctx->err_pending = false;
+    ctx->gemm_err_pending = true;
     ctx->last_paths = paths;
     ctx->last_snap_paths = a.n_snap;
     return LLL_OK;
@@ -700,6 +717,7 @@ int simulate_mlp(lll_ctx *ctx, uint64_t first_path, uint64_t paths, uint64_t see
     if (use_tc) {
         MTRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream));
         ctx->err_pending = true;
+        ctx->gemm_err_pending = false;
     }
     MTRY(cudaEventRecord(ctx->ev[0], ctx->stream));
     if (vec_tc) MTRY(launch_mlp_tc_vec(m->layers, m->in_pad, grid, smem, ctx->stream, a, g));

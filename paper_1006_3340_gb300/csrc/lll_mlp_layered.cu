@@ -27,20 +27,42 @@ namespace {
 
 constexpr int kT = 256; // threads per block of both kernels
 
-// Vector head: one row per path, (t s_t, u_0 .. u_{N-1}).
-__global__ void feat_vec_kernel(const PathArgs a, MlpScales sc, int k, int Pc, const float *state,
-                                __nv_bfloat16 *X, int in_pad)
+// Vector head: one row per path, (t s_t, u_0 .. u_{N-1}), written as
+// 16-byte chunks.  The path state is [rate][path]: a block stages the state of
+// its kFV paths in shared memory (coalesced loads along paths), then writes
+// the BF16 rows chunk by chunk (coalesced stores along a row).
+constexpr int kFV = 32; // paths per block of feat_vec_kernel
+
+__global__ void __launch_bounds__(kT) feat_vec_kernel(const PathArgs a, MlpScales sc, int k, int Pc,
+                                                      const float *state, __nv_bfloat16 *X, int in_pad)
 {
-    const int n = a.n;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= Pc) return;
-    __nv_bfloat16 *x = X + (size_t)p * in_pad;
-    // columns: 0 t, 1 u_0 = 0, 1 + m  u_m (m = 1..n), then zeros
-    x[0] = __float2bfloat16((float)k * a.h * sc.t_scale);
-    x[1] = __float2bfloat16(0.0f);
-    for (int c = 2; c < in_pad; ++c) {
-        const int m = c - 1;
-        x[c] = __float2bfloat16(m <= n ? state[(size_t)(m - 1) * Pc + p] * sc.u_scale : 0.0f);
+    extern __shared__ float fst[]; // [n][kFV + 1]
+    const int n = a.n, p0 = blockIdx.x * kFV;
+    for (int e = threadIdx.x; e < n * kFV; e += kT) {
+        const int m = e / kFV, q = e % kFV;
+        fst[m * (kFV + 1) + q] = p0 + q < Pc ? state[(size_t)m * Pc + p0 + q] * sc.u_scale : 0.0f;
+    }
+    __syncthreads();
+    const float t = (float)k * a.h * sc.t_scale;
+    const int chunks = in_pad / 8;
+    for (int e = threadIdx.x; e < kFV * chunks; e += kT) {
+        const int q = e / chunks, ch = e % chunks;
+        if (p0 + q >= Pc) continue;
+        // columns: 0 t, 1 u_0 = 0, 1 + m  u_m (m = 1..n), then zeros
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int c = ch * 8 + j, m = c - 1;
+            v[j] = c == 0 ? t : ((m >= 1 && m <= n) ? fst[(m - 1) * (kFV + 1) + q] : 0.0f);
+        }
+        uint4 w;
+        __nv_bfloat162 b0 = __floats2bfloat162_rn(v[0], v[1]), b1 = __floats2bfloat162_rn(v[2], v[3]);
+        __nv_bfloat162 b2 = __floats2bfloat162_rn(v[4], v[5]), b3 = __floats2bfloat162_rn(v[6], v[7]);
+        w.x = *reinterpret_cast<uint32_t *>(&b0);
+        w.y = *reinterpret_cast<uint32_t *>(&b1);
+        w.z = *reinterpret_cast<uint32_t *>(&b2);
+        w.w = *reinterpret_cast<uint32_t *>(&b3);
+        *reinterpret_cast<uint4 *>(X + (size_t)(p0 + q) * in_pad + ch * 8) = w;
     }
 }
 
@@ -83,7 +105,7 @@ __device__ __forceinline__ void kahan_add(double *s, double *c, double x)
 // path and live rate), or, for the vector head (outputs > 0), row p column i - 1.
 __global__ void __launch_bounds__(kT) euler_kernel(const PathArgs a, const float *Ctab, float y_scale, int k,
                                                     uint64_t chunk_first, int Pc, float *state,
-                                                    const float *out, int outputs, double *acc)
+                                                    const float *out, int outputs, int out_t, double *acc)
 {
     __shared__ double red[kT / 32][64][2];
     const int n = a.n, s = a.s, ns = a.ns, imin = k / s + 1, live = n - imin + 1;
@@ -97,15 +119,35 @@ __global__ void __launch_bounds__(kT) euler_kernel(const PathArgs a, const float
             sidx = lp / a.snap_stride;
         const float dH = draw_increment(a, a.first_path + lp, (uint32_t)k);
         const float h = a.h;
-        for (int i = n; i >= imin; --i) {
-            const size_t rowk = (size_t)k * n + (i - 1);
-            const size_t oi = outputs > 0 ? (size_t)p * outputs + (i - 1) : (size_t)p * live + (i - imin);
-            const float A = Ctab[rowk] + y_scale * out[oi];
-            float *sp = state + (size_t)(i - 1) * Pc + p;
-            const float z = sp[0] + fmaf(a.row[rowk].x, dH, -A * h);
-            sp[0] = z;
-            if (mat && sidx != ~0ull)
-                a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = z + a.Z0[i - 1];
+        // Rates in batches of 4: every load of a batch is issued before its
+        // stores (the pointers do not alias), so the memory latencies overlap.
+        const float *__restrict__ cr = Ctab + (size_t)k * n;
+        const float4 *__restrict__ rr = a.row + (size_t)k * n;
+        const float *__restrict__ op = out;
+        float *__restrict__ sp = state;
+        for (int i0 = n; i0 >= imin; i0 -= 4) {
+            float o[4], zs[4], c[4], lam[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 - u;
+                if (i < imin) break;
+                const size_t oi = outputs > 0 ? (out_t ? (size_t)(i - 1) * Pc + p : (size_t)p * outputs + (i - 1))
+                                              : (size_t)p * live + (i - imin);
+                o[u] = op[oi];
+                zs[u] = sp[(size_t)(i - 1) * Pc + p];
+                c[u] = cr[i - 1];
+                lam[u] = rr[i - 1].x;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int i = i0 - u;
+                if (i < imin) break;
+                const float A = c[u] + y_scale * o[u];
+                const float z = zs[u] + fmaf(lam[u], dH, -A * h);
+                sp[(size_t)(i - 1) * Pc + p] = z;
+                if (mat && sidx != ~0ull)
+                    a.snap[((size_t)(imin - 1) * n + (i - 1)) * a.snap_pitch + sidx] = z + a.Z0[i - 1];
+            }
         }
     }
     if (!mat) return;
@@ -152,8 +194,10 @@ int launch_mlp_features(const PathArgs &a, const MlpScales &sc, int k, int Pc, c
                         int in_pad, int head, cudaStream_t st)
 {
     if (head) {
-        feat_vec_kernel<<<(Pc + kT - 1) / kT, kT, 0, st>>>(a, sc, k, Pc, state, static_cast<__nv_bfloat16 *>(X),
-                                                           in_pad);
+        if (in_pad % 8) return (int)cudaErrorInvalidValue;
+        const size_t smem = sizeof(float) * (size_t)a.n * (kFV + 1);
+        feat_vec_kernel<<<(Pc + kFV - 1) / kFV, kT, smem, st>>>(a, sc, k, Pc, state,
+                                                                 static_cast<__nv_bfloat16 *>(X), in_pad);
         return (int)cudaGetLastError();
     }
     const int live = a.n - (k / a.s + 1) + 1;
@@ -164,10 +208,11 @@ int launch_mlp_features(const PathArgs &a, const MlpScales &sc, int k, int Pc, c
 }
 
 int launch_mlp_euler(const PathArgs &a, const float *Ctab, float y_scale, int k, uint64_t chunk_first, int Pc,
-                     float *state, const float *out, int outputs, double *acc, cudaStream_t st)
+                     float *state, const float *out, int outputs, int out_t, double *acc, cudaStream_t st)
 {
     if (a.ns > 64) return (int)cudaErrorInvalidValue;
-    euler_kernel<<<(Pc + kT - 1) / kT, kT, 0, st>>>(a, Ctab, y_scale, k, chunk_first, Pc, state, out, outputs, acc);
+    euler_kernel<<<(Pc + kT - 1) / kT, kT, 0, st>>>(a, Ctab, y_scale, k, chunk_first, Pc, state, out, outputs,
+                                                    out_t, acc);
     return (int)cudaGetLastError();
 }
 

@@ -95,6 +95,8 @@ def load():
         "lll_mlp_set_kernel": (I, [V, I]),
         "lll_inject": (I, [V, I]),
         "lll_philox_words": (I, [V, U64, U64, V]),
+        "lll_set_gemm_kernel": (I, [I]),
+        "lll_gemm_bf16": (I, [I, I, I, V, I, V, I, I, I, I, I, V, V, V, V]),
         "lll_measure_pipe_rates": (I, [_dp, I]),
         "lll_batch_init": (I, [ctypes.POINTER(V), I, ctypes.POINTER(lll_instance), V]),
         "lll_batch_set_launch": (I, [V, I, I, I]),
@@ -375,6 +377,27 @@ def lll_philox_words(counters, seed):
     out = np.zeros_like(ctr)
     _check(load().lll_philox_words(ctr.ctypes.data, ctr.shape[0], int(seed) & (2 ** 64 - 1), out.ctypes.data))
     return out
+
+
+def lll_set_gemm_kernel(kind):
+    """Process-wide GEMM kernel of the learned compensator: "tc" (tcgen05, default) or "mma_sync"."""
+    k = {"tc": 0, "mma_sync": 1}.get(kind, kind)
+    _check(load().lll_set_gemm_kernel(int(k)))
+
+
+def lll_gemm_bf16(ta, tb, epi, A_bits, lda, B_bits, ldb, M, N, K, splits=1, bias=None, Zin=None):
+    """One product of the current GEMM kernel on host arrays (uint16 BF16 bits).
+    Returns C [M, N] (FP32) and, for epi 1/2, H [M, N] (uint16 BF16 bits)."""
+    A = np.ascontiguousarray(A_bits, dtype=np.uint16)
+    B = np.ascontiguousarray(B_bits, dtype=np.uint16)
+    C = np.zeros((M, N), dtype=np.float32)
+    H = np.zeros((M, N), dtype=np.uint16) if epi in (1, 2) else None
+    b = np.ascontiguousarray(bias, dtype=np.float32) if bias is not None else None
+    z = np.ascontiguousarray(Zin, dtype=np.float32) if Zin is not None else None
+    ptr = lambda a: a.ctypes.data if a is not None else None  # noqa: E731
+    _check(load().lll_gemm_bf16(int(ta), int(tb), int(epi), ptr(A), int(lda), ptr(B), int(ldb), int(M), int(N),
+                                int(K), int(splits), ptr(b), ptr(z), ptr(C), ptr(H)))
+    return C, H
 
 
 PIPE_RATE_NAMES = ("tanh", "ex2", "rcp", "ffma2_lane_ops", "ffma_lane_ops")

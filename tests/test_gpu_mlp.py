@@ -70,9 +70,14 @@ def _flat_grads(g, offs, in_dim, in_pad):
     return out
 
 
-def test_forward_and_gradients_match_fp64_oracle(lll):
+@pytest.mark.parametrize("gemm", ["tc", "mma_sync"])
+def test_forward_and_gradients_match_fp64_oracle(lll, gemm):
+    """Forward output, loss and every gradient tensor of the GPU training pass
+    (GEMMs on the tcgen05 kernel, the default, or the mma.sync kernel) against
+    the FP64 oracle on the same BF16 weights and inputs."""
     wl = workloads.large_single(paths=1024)
     sim = lll.LevyLibor(wl)
+    lll.lll_set_gemm_kernel(gemm)
     try:
         lll.lll_mlp_init(sim.ctx, H, L, seed=3)
         n_params, in_dim, in_pad, offs = lll.lll_mlp_layout(sim.ctx, L)
@@ -83,6 +88,7 @@ def test_forward_and_gradients_match_fp64_oracle(lll):
         y = rng.normal(size=rows).astype(np.float32)
         out, g, loss = lll.lll_mlp_eval(sim.ctx, x, y, n_params, want_grads=True)
     finally:
+        lll.lll_set_gemm_kernel("tc")
         sim.close()
     params = _oracle_params(flat, offs, in_dim, in_pad)
     out_o, _ = omlp.forward(params, x.astype(np.float64))

@@ -32,9 +32,11 @@ def lll():
     return mod
 
 
-def test_vector_head_forward_and_gradients_match_fp64(lll):
+@pytest.mark.parametrize("gemm", ["tc", "mma_sync"])
+def test_vector_head_forward_and_gradients_match_fp64(lll, gemm):
     wl = workloads.large_single(paths=1024)
     sim = lll.LevyLibor(wl)
+    lll.lll_set_gemm_kernel(gemm)
     try:
         lll.lll_mlp_init(sim.ctx, H, L, seed=5, head=1)
         head, O = lll.lll_mlp_shape(sim.ctx)
@@ -48,6 +50,7 @@ def test_vector_head_forward_and_gradients_match_fp64(lll):
         y = rng.normal(size=(rows, O)).astype(np.float32)
         out, g, loss = lll.lll_mlp_eval(sim.ctx, x, y, n_params, want_grads=True)
     finally:
+        lll.lll_set_gemm_kernel("tc")
         sim.close()
     params = omlp.params_from_flat(flat, offs, L, H, in_dim, in_pad, outputs=O)
     out_o = omlp.forward_vec(params, x.astype(np.float64))
