@@ -48,9 +48,24 @@ def _arch(wl):
 
 
 def _schemes(args):
+    """Default schemes: the N=40 workload runs the per-rate learned drift of its
+    43->128x3->1 network; the N=120 workload runs its learned drift as the
+    vector head 121->256x4->119 (one pass per path and step, the network's
+    input being t and the 120 log-rates)."""
     if args.schemes:
         return [s for s in args.schemes.split(",") if s]
-    return ["picard", "full"] if args.workload == "long_dated" else ["picard", "full", "mlp"]
+    return ["picard", "full", "mlp_vec"] if args.workload == "long_dated" else ["picard", "full", "mlp"]
+
+
+def _train_flop(wl, hid, lay, head, n_params, epochs, batch, train_paths=1 << 16, records=8):
+    """Floating-point operations of the GPU training run: Adam steps x rows x
+    6 x (multiply-adds of the network) -- forward 2, backward 4 per weight
+    (dX and dW); the library takes max(1, pairs / batch) steps per epoch, with
+    pairs = records x (n + 1) / 2 per recorded step (per-rate head) or the
+    records themselves (vector head)."""
+    nrec = train_paths * records
+    per_epoch = max(1, int((nrec if head else nrec * (wl.n + 1) / 2.0) // batch))
+    return per_epoch * epochs * batch * 6.0 * n_params
 
 
 def _code(s):
@@ -403,7 +418,7 @@ def _alu_peaks(lll, torch, dev, rates=None):
 
 
 def run_single(args, wl, schemes, steps, warmup, dev, rank, world, local, with_cpu=True, with_e2e=True,
-               rates=None, tune=True):
+               rates=None, tune=True, tune_candidates=None, tune_repeats=2):
     """One term structure: every scheme simulates all paths of the workload per
     step.  Returns the JSON line (rank 0) or None."""
     import torch
@@ -426,14 +441,22 @@ def run_single(args, wl, schemes, steps, warmup, dev, rank, world, local, with_c
         # The learned compensator is trained once, on its own paths (seed 7),
         # with the project's GPU kernels; the timed steps then price with it.
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("train")
         t0 = time.perf_counter()
         loss = lll.lll_mlp_train(sims["mlp"].ctx, hidden=hid, layers=lay, train_paths=1 << 16,
                                  records_per_path=8, epochs=4, batch=8192, lr=2e-3, lr_final=1e-4, seed=7)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         lll.lll_mlp_set_kernel(sims["mlp"].ctx, args.mlp_kernel)
         n_params, in_dim, in_pad, offs = lll.lll_mlp_layout(sims["mlp"].ctx, lay)
         mlp_params = lll.lll_mlp_params(sims["mlp"].ctx, 0, count=n_params)
-        mlp_info = {"train_s": time.perf_counter() - t0, "final_loss_scaled": loss, "params": int(n_params),
+        train_s = time.perf_counter() - t0
+        tflop = _train_flop(wl, hid, lay, 0, n_params, 4, 8192)
+        mlp_info = {"train_s": train_s, "final_loss_scaled": loss, "params": int(n_params),
+                    "train_tflops": tflop / train_s / 1e12,
+                    "train_tflops_frac": tflop / train_s / 1e12 / float(_peaks().get("bf16_tflops_sustained", 1679.9)),
+                    "train_flop_basis": "Adam steps x 8192 rows x 6 x params over the whole lll_mlp_train call "
+                                        "(data generation by the quadrature full scheme included); GEMMs on tcgen05",
                     "s_y": float(mlp_params[1][4]),
                     "arch": f"{in_dim}->{hid}x{lay}->1 SiLU, BF16 weights, FP32 accumulate",
                     "train_pairs": "2^16 paths x 8 recorded steps x live rates (~1e7)"}
@@ -445,15 +468,23 @@ def run_single(args, wl, schemes, steps, warmup, dev, rank, world, local, with_c
     if "mlp_vec" in schemes:
         # the vector-head network: one pass per path and step gives every rate's compensator
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("train_vec")
         t0 = time.perf_counter()
+        ep_v = 40 if hid == 128 else 20
         lossv = lll.lll_mlp_train(sims["mlp_vec"].ctx, hidden=hid, layers=lay, train_paths=1 << 16,
-                                  records_per_path=8, epochs=40 if hid == 128 else 20, batch=4096, lr=2e-3,
+                                  records_per_path=8, epochs=ep_v, batch=4096, lr=2e-3,
                                   lr_final=1e-4, seed=7, head=1)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        train_s_v = time.perf_counter() - t0
         nv, in_dim_v, in_pad_v, offs_v = lll.lll_mlp_layout(sims["mlp_vec"].ctx, lay)
         _, vec_out = lll.lll_mlp_shape(sims["mlp_vec"].ctx)
         mlp_vec_params = lll.lll_mlp_params(sims["mlp_vec"].ctx, 0, count=nv)
-        mlp_info = dict(mlp_info or {}, vec={"train_s": time.perf_counter() - t0, "final_loss_scaled": lossv,
+        tflop_v = _train_flop(wl, hid, lay, 1, nv, ep_v, 4096)
+        mlp_info = dict(mlp_info or {}, vec={"train_s": train_s_v, "final_loss_scaled": lossv,
+                                              "train_tflops": tflop_v / train_s_v / 1e12,
+                                              "train_tflops_frac": tflop_v / train_s_v / 1e12 /
+                                              float(_peaks().get("bf16_tflops_sustained", 1679.9)),
                                               "params": int(nv), "s_y": float(mlp_vec_params[1][4]),
                                               "arch": f"{in_dim_v}->{hid}x{lay}->{vec_out} SiLU (vector head), "
                                                       f"BF16, FP32 acc",
@@ -483,11 +514,11 @@ def run_single(args, wl, schemes, steps, warmup, dev, rank, world, local, with_c
                 tuned[s] = {"launch(threads,bps,chunk,ppt,lanes[,tenor])": shape, "ms": None}
     elif tune:
         # one lane per path (paths per thread 1 or 2), and the tenor-parallel mapping
-        cands = [(128, 0, 0, 1, 1), (256, 0, 0, 1, 1), (128, 0, 0, 1, 2), (256, 0, 0, 1, 2),
-                 (0, 0, 0, 0, 0, 8), (0, 0, 0, 0, 0, 16)]
+        cands = tune_candidates or [(128, 0, 0, 1, 1), (256, 0, 0, 1, 1), (128, 0, 0, 1, 2), (256, 0, 0, 1, 2),
+                                    (0, 0, 0, 0, 0, 8), (0, 0, 0, 0, 0, 16)]
         for s in schemes:
             if s in ("picard", "full", "frozen"):
-                r = autotune.tune(sims[s], s, candidates=cands, repeats=2, use_cache=False)
+                r = autotune.tune(sims[s], s, candidates=cands, repeats=tune_repeats, use_cache=False)
                 tuned[s] = {"launch(threads,bps,chunk,ppt,lanes[,tenor])": r["launch"], "ms": r["ms"]}
 
     for _ in range(warmup):
@@ -732,7 +763,7 @@ def run_mappings(args, rates=None):
 def _extra_block(line):
     """The figures of another configuration kept in the headline line."""
     keep = ("value", "unit", "ms_per_step", "steps", "warmup", "config", "per_scheme", "caplets_per_s",
-            "roofline", "roofline_picard", "roofline_mlp", "autotuned", "clocks", "mlp")
+            "roofline", "roofline_picard", "roofline_mlp", "roofline_mlp_vec", "autotuned", "clocks", "mlp")
     return {k: line[k] for k in keep if k in line}
 
 
@@ -798,9 +829,11 @@ def main():
             # the other single-GPU configurations, a few steps each, in the same line
             extra = {"batch256": _extra_block(run_batch(args, 2, 1, False, False, rates))}
             wl5 = workloads.long_dated()
+            # two one-lane shapes (a launch of this workload takes about 1.7 s)
             extra["long_dated"] = _extra_block(run_single(
-                args, wl5, ["picard", "full"], 2, 1, dev, rank, world, local, with_cpu=False, with_e2e=False,
-                rates=rates, tune=True))
+                args, wl5, ["picard", "full", "mlp_vec"], 2, 1, dev, rank, world, local, with_cpu=False,
+                with_e2e=False, rates=rates, tune=True, tune_candidates=[(128, 0, 0, 1, 1), (256, 0, 0, 1, 1)],
+                tune_repeats=1))
             line["extra_configs"] = extra
     if line is not None:
         print(json.dumps(line), flush=True)

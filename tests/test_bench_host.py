@@ -39,7 +39,7 @@ def test_workload_dispatch_and_network_shape():
 def test_default_schemes():
     b = _bench()
     assert b._schemes(_args()) == ["picard", "full", "mlp"]
-    assert b._schemes(_args(workload="long_dated")) == ["picard", "full"]
+    assert b._schemes(_args(workload="long_dated")) == ["picard", "full", "mlp_vec"]
     assert b._schemes(_args(schemes="picard,mlp_vec")) == ["picard", "mlp_vec"]
     assert b._code("mlp_vec") == "mlp" and b._code("full") == "full"
 
@@ -55,3 +55,15 @@ def test_batched_recipe():
     assert len({wl.N for wl in wls}) > 40
     budgets = np.array([wl.paths for wl in wls])
     assert budgets.max() > 20 * budgets.min()
+
+
+def test_training_flop_count():
+    """6 x params per training row (forward 2, backward 4) over the library's
+    Adam steps: per-rate head, pairs = records x (n + 1) / 2 per step."""
+    b = _bench()
+    wl = workloads.large_single()
+    f = b._train_flop(wl, 128, 3, 0, 39432, 4, 8192)
+    steps = int((1 << 16) * 8 * 20 // 8192) * 4
+    assert f == steps * 8192 * 6.0 * 39432
+    fv = b._train_flop(workloads.long_dated(), 256, 4, 1, 263296, 20, 4096)
+    assert fv == ((1 << 16) * 8 // 4096) * 20 * 4096 * 6.0 * 263296
