@@ -515,7 +515,7 @@ def run_single(args, wl, schemes, steps, warmup, dev, rank, world, local, with_c
     elif tune:
         # one lane per path (paths per thread 1 or 2), and the tenor-parallel mapping
         cands = tune_candidates or [(128, 0, 0, 1, 1), (256, 0, 0, 1, 1), (128, 0, 0, 1, 2), (256, 0, 0, 1, 2),
-                                    (0, 0, 0, 0, 0, 8), (0, 0, 0, 0, 0, 16)]
+                                    (0, 0, 0, 0, 0, 8), (0, 0, 0, 0, 0, 16), (0, 0, 0, 0, 0, -1)]
         for s in schemes:
             if s in ("picard", "full", "frozen"):
                 r = autotune.tune(sims[s], s, candidates=cands, repeats=tune_repeats, use_cache=False)
@@ -734,7 +734,8 @@ def run_mappings(args, rates=None):
     pk = _alu_peaks(lll, torch, dev, rates)
     shapes = [("path, 128 threads", (128, 0, 0, 1, 1)), ("path, 256 threads", (256, 0, 0, 1, 1)),
               ("path, 2 paths/thread", (128, 0, 0, 2, 1))] + \
-             [(f"tenor, {g} lanes/path", (0, 0, 0, 0, 0, g)) for g in (4, 8, 16, 32)]
+             [(f"tenor, {g} lanes/path", (0, 0, 0, 0, 0, g)) for g in (4, 8, 16, 32)] + \
+             [("step-parallel (Picard)", (0, 0, 0, 0, 0, -1))]
     rows = []
     for paths in (1 << 20, 1 << 12):
         wl = workloads.large_single(paths=paths)
@@ -743,6 +744,8 @@ def run_mappings(args, rates=None):
         try:
             for scheme in ("picard", "full"):
                 for name, cand in shapes:
+                    if scheme == "full" and len(cand) > 5 and cand[5] < 0:
+                        continue  # the full scheme's steps are sequential
                     autotune.apply(sim, cand)
                     sim.simulate(scheme)  # warm-up
                     ms = []

@@ -176,9 +176,22 @@ int lll_set_launch(lll_ctx *ctx, int threads_per_block, int blocks_per_sm, int c
  *     5/3 of the one-lane arithmetic plus the scan, for `lanes` times the
  *     threads per path: for small path budgets.  128-thread blocks; caplet
  *     payoffs and a node table only (LLL_EUNSUPPORTED otherwise at simulation).
+ *   LLL_MAP_STEP (2, Picard only; `lanes` ignored): the Euler steps of a path
+ *     evaluated in parallel.  Under Eq. (Picard-2) the drift at t_k reads
+ *     Z^(1)(t_k), a function of the driving path alone, so after a prefix
+ *     sum of lambda_l Delta H over the steps, one thread per (step, path) runs
+ *     the suffix sweep of that step, and a second prefix sum over the steps
+ *     gives the log-rates at every maturity.  Same arithmetic per unit as the
+ *     path mapping; intermediate arrays of about 4 (S + 2 S n + n^2) bytes per
+ *     path, processed in chunks within 2 GiB of device memory.  For small
+ *     path budgets (a single term structure of 2^12 paths).  LLL_FULL
+ *     returns LLL_EUNSUPPORTED under it: the full scheme's drift reads the
+ *     simulated rates, so its steps are sequential.  lll_simulate_noalloc
+ *     ignores it (path mapping).
  * Other schemes ignore the mapping. */
 #define LLL_MAP_PATH 0
 #define LLL_MAP_TENOR 1
+#define LLL_MAP_STEP 2
 int lll_set_mapping(lll_ctx *ctx, int mapping, int lanes);
 
 /* lll_kernel_ms -- device time of the last simulation's path kernel and of the

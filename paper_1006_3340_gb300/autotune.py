@@ -24,15 +24,19 @@ CACHE = os.path.join(_build.BUILD, "autotune.json")
 DEFAULT_CANDIDATES = [
     # (threads, blocks_per_sm, chunk_rows, paths_per_thread, lanes_per_path[, tenor lanes])
     (t, 0, c, 1, l) for t, c, l in itertools.product((64, 128, 256), (0, 16), (1, 4))
-] + [(0, 0, 0, 0, 0, g) for g in (4, 8, 16, 32)]
+] + [(0, 0, 0, 0, 0, g) for g in (4, 8, 16, 32, -1)]
 
 
 def apply(sim: "lll.LevyLibor", cand) -> None:
     """Set a candidate: the five launch values, then the mapping (sixth value,
-    0 or absent: one lane per path; G: tenor-parallel with G lanes per path)."""
+    0 or absent: one lane per path; G > 0: tenor-parallel with G lanes per
+    path; -1: Picard's step-parallel mapping)."""
     sim.set_launch(*cand[:5])
     g = cand[5] if len(cand) > 5 else 0
-    sim.set_mapping("tenor" if g else "path", g)
+    if g < 0:
+        sim.set_mapping("step")
+    else:
+        sim.set_mapping("tenor" if g else "path", g)
 
 
 def _gpu_name() -> str:

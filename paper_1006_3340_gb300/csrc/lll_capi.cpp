@@ -386,14 +386,93 @@ int lll_set_mapping(lll_ctx *ctx, int mapping, int lanes)
     if (!ctx) return fail(nullptr, LLL_EINVAL, "ctx is NULL");
     if (mapping == LLL_MAP_PATH) {
         ctx->tenor_lanes = 0;
+        ctx->step_map = false;
+        return LLL_OK;
+    }
+    if (mapping == LLL_MAP_STEP) {
+        ctx->tenor_lanes = 0;
+        ctx->step_map = true;
         return LLL_OK;
     }
     if (mapping != LLL_MAP_TENOR) return fail(ctx, LLL_EINVAL, "unknown mapping");
     if (lanes != 4 && lanes != 8 && lanes != 16 && lanes != 32)
         return fail(ctx, LLL_EINVAL, "lanes must be 4, 8, 16 or 32");
     ctx->tenor_lanes = lanes;
+    ctx->step_map = false;
     return LLL_OK;
 }
+
+}  // extern "C"
+
+namespace {
+
+// The Picard scheme with its Euler steps in parallel (lll_paths_step.cu):
+// chunks of paths through the five kernels, then the fixed-order block sum.
+int simulate_step(lll_ctx *ctx, uint64_t first_path, uint64_t paths, uint64_t seed)
+{
+    LaunchPlan plan;
+    int rc = plan_launch(ctx, LLL_PICARD, first_path, paths, seed, &plan, false);
+    if (rc != LLL_OK) return rc;
+    if (plan.qp == 0 || !step_kernels_supported(plan.qp, ctx->ns))
+        return fail(ctx, LLL_EUNSUPPORTED, "the step-parallel mapping needs a node table and at most 64 strikes");
+    const int n = ctx->n, S = ctx->S;
+    // intermediate arrays of about 4 (S + 2 S n + n^2) bytes per path: chunks within 2 GiB
+    const size_t per_path = step_bytes_per_path(n, S);
+    uint64_t Pc = std::max<uint64_t>(128, ((size_t(1) << 31) / per_path) / 128 * 128);
+    Pc = std::min<uint64_t>(Pc, paths);
+    const size_t floats = per_path / 4 * Pc;
+    if (floats > ctx->state_cap) {
+        cudaFree(ctx->d_state);
+        ctx->d_state = nullptr;
+        ctx->state_cap = 0;
+        if (dalloc(&ctx->d_state, floats) != cudaSuccess) return fail(ctx, LLL_ENOMEM, "step-parallel scratch");
+        ctx->state_cap = floats;
+    }
+    int blocks = 0;
+    for (uint64_t c0 = 0; c0 < paths; c0 += Pc) blocks += step_blocks_per_chunk((int)std::min<uint64_t>(Pc, paths - c0));
+    const size_t nout = (size_t)plan.n_out;
+    if ((size_t)blocks * nout > ctx->partials_cap) {
+        cudaFree(ctx->d_partials);
+        ctx->d_partials = nullptr;
+        ctx->partials_cap = 0;
+        if (dalloc(&ctx->d_partials, (size_t)blocks * nout) != cudaSuccess) return fail(ctx, LLL_ENOMEM, "partials");
+        ctx->partials_cap = (size_t)blocks * nout;
+    }
+    if (nout > ctx->sums_cap) {
+        cudaFree(ctx->d_sums);
+        ctx->d_sums = nullptr;
+        ctx->sums_cap = 0;
+        if (dalloc(&ctx->d_sums, nout) != cudaSuccess) return fail(ctx, LLL_ENOMEM, "sums");
+        ctx->sums_cap = nout;
+    }
+    PathArgs a = plan.args;
+    a.snap = ctx->d_snap; a.snap_stride = ctx->snap_stride; a.snap_pitch = ctx->n_snap;
+    a.n_snap = ctx->d_snap ? std::min<uint64_t>(ctx->n_snap, (paths + ctx->snap_stride - 1) / ctx->snap_stride) : 0;
+    float *dH = ctx->d_state, *Y = dH + (size_t)S * Pc, *Bh = Y + (size_t)S * n * Pc, *Zm = Bh + (size_t)S * n * Pc;
+    CUDA_TRY(ctx, cudaEventRecord(ctx->ev[0], ctx->stream));
+    int block0 = 0;
+    for (uint64_t c0 = 0; c0 < paths; c0 += Pc) {
+        const int pc = (int)std::min<uint64_t>(Pc, paths - c0);
+        const cudaError_t e = (cudaError_t)launch_step_chunk(plan.qp, a, c0, pc, dH, Y, Bh, Zm, block0,
+                                                             ctx->d_partials, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "step-parallel kernels");
+        block0 += step_blocks_per_chunk(pc);
+    }
+    CUDA_TRY(ctx, cudaEventRecord(ctx->ev[1], ctx->stream));
+    const cudaError_t e = (cudaError_t)launch_finalize(ctx->d_partials, blocks, (int)nout, ctx->d_sums, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "finalize launch");
+    CUDA_TRY(ctx, cudaEventRecord(ctx->ev[2], ctx->stream));
+    ctx->simulated = true;
+    ctx->err_pending = false;
+    ctx->gemm_err_pending = false;
+    ctx->last_paths = paths;
+    ctx->last_snap_paths = a.n_snap;
+    return LLL_OK;
+}
+
+}  // namespace
+
+extern "C" {
 
 int lll_simulate(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, uint64_t seed)
 {
@@ -405,6 +484,14 @@ int lll_simulate(lll_ctx *ctx, int scheme, uint64_t first_path, uint64_t paths, 
         if (ctx->ns == 0) return fail(ctx, LLL_ESTATE, "lll_set_strikes must come before lll_simulate");
         if (paths == 0) return fail(ctx, LLL_EINVAL, "paths must be > 0");
         return simulate_expand(ctx, scheme == LLL_EXPAND1 ? 1 : 2, first_path, paths, seed);
+    }
+    if (ctx && ctx->step_map && (scheme == LLL_PICARD || scheme == LLL_FULL)) {
+        if (scheme == LLL_FULL)
+            return fail(ctx, LLL_EUNSUPPORTED,
+                        "the step-parallel mapping is Picard's: the full scheme's drift reads the simulated rates");
+        if (ctx->ns == 0) return fail(ctx, LLL_ESTATE, "lll_set_strikes must come before lll_simulate");
+        if (paths == 0) return fail(ctx, LLL_EINVAL, "paths must be > 0");
+        return simulate_step(ctx, first_path, paths, seed);
     }
     LaunchPlan plan;
     int rc = plan_launch(ctx, scheme, first_path, paths, seed, &plan);

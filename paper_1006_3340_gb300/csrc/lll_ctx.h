@@ -40,6 +40,7 @@ struct lll_ctx {
     uint64_t last_snap_paths = 0;
     int threads = 128, blocks_per_sm = 0, chunk_rows = 0, ppt = 0, lpp = 0; // 0: automatic
     int tenor_lanes = 0; // > 0: full and Picard on the tenor-parallel kernel (lll_set_mapping)
+    bool step_map = false; // Picard with its Euler steps in parallel (lll_set_mapping)
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
     std::vector<double> lam; // host copy of lambda [S][n]
     lll::MlpState *mlp = nullptr;

@@ -87,6 +87,12 @@ size_t tenor_kernel_smem(int QP, int n, int ns, int G);
 int tenor_kernel_threads();
 int tenor_kernel_prepare(int scheme, int QP, int G, size_t smem, int *blocks_per_sm);
 int launch_tenor_kernel(int scheme, int QP, int G, int grid, size_t smem, cudaStream_t st, const PathArgs &a);
+// Launchers implemented in lll_paths_step.cu (Picard with its Euler steps in parallel).
+bool step_kernels_supported(int QP, int ns);
+size_t step_bytes_per_path(int n, int S);
+int step_blocks_per_chunk(int Pc);
+int launch_step_chunk(int QP, const PathArgs &a, uint64_t chunk_first, int Pc, float *dH, float *Y, float *Bh,
+                      float *Zm, int block0, double *partials, cudaStream_t st);
 struct LaunchPlan;
 int launch_plan(const LaunchPlan &plan, const PathArgs &a);
 bool batch_kernel_supported(int scheme, int QP);

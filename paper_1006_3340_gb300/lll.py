@@ -208,12 +208,13 @@ def lll_set_launch(ctx, threads=0, blocks_per_sm=0, chunk_rows=0, paths_per_thre
                                  int(paths_per_thread), int(lanes_per_path)), ctx)
 
 
-LLL_MAP_PATH, LLL_MAP_TENOR = 0, 1
+LLL_MAP_PATH, LLL_MAP_TENOR, LLL_MAP_STEP = 0, 1, 2
 
 
 def lll_set_mapping(ctx, mapping, lanes=0):
-    """mapping: "path" (one lane per path) or "tenor" (``lanes`` lanes per path)."""
-    m = {"path": LLL_MAP_PATH, "tenor": LLL_MAP_TENOR}.get(mapping, mapping)
+    """mapping: "path" (one lane per path), "tenor" (``lanes`` lanes per path) or
+    "step" (Picard: the Euler steps of a path in parallel)."""
+    m = {"path": LLL_MAP_PATH, "tenor": LLL_MAP_TENOR, "step": LLL_MAP_STEP}.get(mapping, mapping)
     _check(load().lll_set_mapping(ctx, int(m), int(lanes)), ctx)
 
 

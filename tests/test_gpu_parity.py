@@ -145,3 +145,70 @@ def test_tenor_mapping_refuses_swaptions_and_keeps_other_schemes(lll):
         sim.simulate("picard")
     finally:
         sim.close()
+
+
+# Step-parallel mapping of the Picard scheme (lll_set_mapping("step")): the
+# Euler steps of a path evaluated in parallel from prefix sums of lambda dH.
+@pytest.mark.parametrize("maker,paths", [(workloads.small_plain, 3001), (workloads.large_single, 1037),
+                                         (workloads.long_dated, 100)])
+def test_step_mapping_picard_matches_oracle(lll, maker, paths):
+    wl = maker(paths=paths) if maker is not workloads.large_single else maker()
+    x, W = quadrature.rule_for(wl)
+    sim = lll.LevyLibor(wl, x, W)
+    try:
+        sim.set_mapping("step")
+        sim.simulate("picard", paths=paths, snapshots=paths)
+        zg = sim.paths(0, paths).astype(np.float64)
+        pg, _ = sim.prices()
+    finally:
+        sim.close()
+    ref = ora.simulate(ora.OracleModel(wl, x, W), ora.PICARD, npaths=paths, want_snap=True)
+    mask = ~np.isnan(ref["snap"])
+    assert np.array_equal(mask, ~np.isnan(zg))
+    assert np.abs(np.expm1(zg[mask] - ref["snap"][mask])).max() <= REL_RATE
+    assert np.abs(pg - ref["price"]).max() <= ABS_PRICE
+
+
+@pytest.mark.parametrize("N,s,Q,paths", [(2, 1, 8, 1), (3, 2, 8, 33), (7, 4, 40, 129)])
+def test_step_mapping_tiny_edge_shapes(lll, N, s, Q, paths):
+    wl = workloads.tiny(N=N, s=s, Q=Q, paths=paths)
+    x, W = quadrature.rule_for(wl)
+    sim = lll.LevyLibor(wl, x, W)
+    try:
+        sim.set_mapping("step")
+        sim.simulate("picard", paths=paths, snapshots=paths)
+        zg = sim.paths(0, paths).astype(np.float64)
+        pg, _ = sim.prices()
+    finally:
+        sim.close()
+    ref = ora.simulate(ora.OracleModel(wl, x, W), ora.PICARD, npaths=paths, want_snap=True)
+    mask = ~np.isnan(ref["snap"])
+    assert np.abs(np.expm1(zg[mask] - ref["snap"][mask])).max() <= REL_RATE
+    assert np.abs(pg - ref["price"]).max() <= ABS_PRICE
+
+
+def test_step_mapping_equals_path_mapping_across_chunks(lll):
+    """50,001 paths of the N=40 workload take three chunks of the step-parallel
+    pipeline (20,480 paths each).  Each unit does the path kernel's arithmetic
+    in the same order, so every recorded log-rate is bit-equal to the path
+    mapping's and the prices differ only by the payoff reduction order."""
+    wl = workloads.large_single(paths=50001)
+    x, W = quadrature.rule_for(wl)
+    sim = lll.LevyLibor(wl, x, W)
+    try:
+        sim.set_launch(128, 0, 0, 1, 1)
+        sim.simulate("picard", snapshots=200, snapshot_stride=250)
+        z_path = sim.paths(0, 200)
+        p_path, _ = sim.prices()
+        sim.set_mapping("step")
+        sim.simulate("picard", snapshots=200, snapshot_stride=250)
+        z_step = sim.paths(0, 200)
+        p_step, _ = sim.prices()
+        with pytest.raises(lll.LLLError) as e:
+            sim.simulate("full")
+        assert e.value.code == lll.LLL_EUNSUPPORTED
+    finally:
+        sim.close()
+    mask = ~np.isnan(z_path)
+    assert np.array_equal(z_path[mask], z_step[mask])
+    assert np.allclose(p_step, p_path, rtol=1e-12, atol=1e-18)
