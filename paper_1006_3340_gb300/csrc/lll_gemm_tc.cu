@@ -44,7 +44,7 @@ namespace lll {
 namespace {
 
 constexpr int kM = 128;                      // rows per CTA tile (TMEM lanes)
-constexpr int kWsMinRows = 16384;            // streamed rows from which the weight-stationary kernel is used
+constexpr int kWsMinRows = 8192;             // streamed rows from which the weight-stationary kernel is used
 constexpr int kThreadsG = 128;
 constexpr long long kWaitBudgetG = 4000000000ll; // clock cycles (about 2 s)
 
@@ -314,7 +314,6 @@ __global__ void __launch_bounds__(kThreadsG) gemm_tc(const GemmArgs g)
 #pragma unroll
                     for (int j = 0; j < 16; ++j) r[j] = 0u;
                 }
-                const size_t orow = (size_t)min(m0 + rloc, g.M - 1) * g.N;
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int cl = c16 + j, gn = n0 + cg0 + cl;
@@ -322,14 +321,59 @@ __global__ void __launch_bounds__(kThreadsG) gemm_tc(const GemmArgs g)
                     float f = v;
                     if (EPI == 1 || EPI == 3) f = v + (gn < g.N ? g.bias[gn] : 0.0f);
                     if (EPI == 4) f = v + (m0 + rloc < g.M ? g.bias[m0 + rloc] : 0.0f);
-                    if (EPI == 2) f = v * ((gn < g.N && m0 + rloc < g.M) ? silu_grad(g.Zin[orow + gn]) : 0.0f);
+                    // epilogue 2 applies SiLU'(Zin) in the copy-out below, where Zin is
+                    // read along rows (coalesced)
                     sf[rloc * FP + cl] = f;
                     if (EPI == 1) sh[rloc * HP + cl] = __float2bfloat16(silu(f));
-                    if (EPI == 2) sh[rloc * HP + cl] = __float2bfloat16(f);
                 }
             }
             __syncthreads();
             const int rows = min(kM, g.M - m0), cols = min(CG, g.N - n0 - cg0);
+            if (EPI == 2) {
+                // d = C SiLU'(Zin): FP32 to Zout and BF16 to Hout along rows
+                // (consecutive threads, consecutive 4-column chunks); four chunks per
+                // thread are loaded before any is used, so the loads overlap
+                if (vecf && cols == CG) {
+                    constexpr int CH = CG / 4;
+                    for (int q0 = tid; q0 < rows * CH; q0 += 4 * kThreadsG) {
+                        float4 z[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int q = q0 + u * kThreadsG;
+                            if (q < rows * CH)
+                                z[u] = __ldg(reinterpret_cast<const float4 *>(
+                                    g.Zin + (size_t)(m0 + q / CH) * g.N + n0 + cg0 + (q % CH) * 4));
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int q = q0 + u * kThreadsG;
+                            if (q >= rows * CH) break;
+                            const int rr = q / CH, cc = (q % CH) * 4;
+                            const size_t o = (size_t)(m0 + rr) * g.N + n0 + cg0 + cc;
+                            const float4 a = *reinterpret_cast<const float4 *>(sf + rr * FP + cc);
+                            const float4 d = make_float4(a.x * silu_grad(z[u].x), a.y * silu_grad(z[u].y),
+                                                         a.z * silu_grad(z[u].z), a.w * silu_grad(z[u].w));
+                            *reinterpret_cast<float4 *>(g.Zout + o) = d;
+                            const __nv_bfloat162 h0 = __floats2bfloat162_rn(d.x, d.y), h1 = __floats2bfloat162_rn(d.z, d.w);
+                            uint2 hw;
+                            hw.x = *reinterpret_cast<const uint32_t *>(&h0);
+                            hw.y = *reinterpret_cast<const uint32_t *>(&h1);
+                            *reinterpret_cast<uint2 *>(g.Hout + o) = hw;
+                        }
+                    }
+                } else {
+                    for (int q = tid; q < rows * CG; q += kThreadsG) {
+                        const int rr = q / CG, cc = q % CG;
+                        if (cc >= cols) continue;
+                        const size_t o = (size_t)(m0 + rr) * g.N + n0 + cg0 + cc;
+                        const float d = sf[rr * FP + cc] * silu_grad(g.Zin[o]);
+                        g.Zout[o] = d;
+                        g.Hout[o] = __float2bfloat16(d);
+                    }
+                }
+                __syncthreads();
+                continue;
+            }
             const bool want_f = EPI != 1 || g.Zout != nullptr;
             if (want_f) {
                 if (vecf) {
@@ -346,7 +390,7 @@ __global__ void __launch_bounds__(kThreadsG) gemm_tc(const GemmArgs g)
                     }
                 }
             }
-            if (EPI == 1 || EPI == 2) {
+            if (EPI == 1) {
                 if (vech) {
                     for (int q = tid; q < rows * (CG / 8); q += kThreadsG) {
                         const int rr = q / (CG / 8), cc = (q % (CG / 8)) * 8;
@@ -772,6 +816,7 @@ int mlp_gemm_tc(int ta, int tb, int epi, const void *A, int lda, const void *B, 
     if (epi == 0 && ta == 0 && tb == 1) return launch_nt<0, 1, 0>(NT, grid, st, g);
     if (epi == 1 && ta == 0 && tb == 1) return launch_nt<0, 1, 1>(NT, grid, st, g);
     if (epi == 2 && ta == 0 && tb == 0) return launch_nt<0, 0, 2>(NT, grid, st, g);
+    if (epi == 2 && ta == 0 && tb == 1) return launch_nt<0, 1, 2>(NT, grid, st, g);
     if (epi == 3 && ta == 0 && tb == 1) return launch_nt<0, 1, 3>(NT, grid, st, g);
     if (epi == 4 && ta == 0 && tb == 1) return launch_nt<0, 1, 4>(NT, grid, st, g);
     return (int)cudaErrorInvalidValue;
@@ -804,7 +849,8 @@ extern "C" int lll_gemm_bf16(int ta, int tb, int epi, const uint16_t *A, int lda
         return record_error(nullptr, LLL_EINVAL, "null buffer or non-positive size");
     if ((epi == 1 && (!bias || !H)) || (epi == 2 && (!Zin || !H)) || (epi >= 3 && !bias) || epi < 0 || epi > 4)
         return record_error(nullptr, LLL_EINVAL, "epilogue 1 needs bias and H, 2 Zin and H, 3 and 4 bias");
-    if ((epi == 0 && tb == 1 && ta == 1) || ((epi == 1 || epi >= 3) && (ta || !tb)) || (epi == 2 && (ta || tb)))
+    if ((epi == 0 && tb == 1 && ta == 1) || ((epi == 1 || epi >= 3) && (ta || !tb)) || (epi == 2 && ta) ||
+        (epi == 2 && tb && g_gemm_kind != LLL_GEMM_TC))
         return record_error(nullptr, LLL_EUNSUPPORTED, "operand layout not used with this epilogue");
     if (epi >= 3 && g_gemm_kind != LLL_GEMM_TC)
         return record_error(nullptr, LLL_EUNSUPPORTED, "epilogues 3 and 4 are tcgen05 only");

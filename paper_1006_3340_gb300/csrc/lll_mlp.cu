@@ -244,52 +244,84 @@ __global__ void out_backward(const float *dout, const __nv_bfloat16 *w, const fl
     dZh[e] = __float2bfloat16(d);
 }
 
-// grad_w_out[c] = sum_r dout[r] H[r, c]; grad_b_out = sum_r dout[r]  (one block per column
-// plus one for the bias; fixed-order reduction).
-__global__ void out_weight_grad(const float *dout, const __nv_bfloat16 *H, int rows, int Hdim,
-                                float *gw, float *gb)
+// Column sums in two fixed-order passes (bias and output-weight gradients):
+// pass 1, block (32-column group, chunk of kColRows rows), 32 x 8 threads:
+// thread (c, y) adds rows y, y + 8, .. of the chunk in column c (a warp reads
+// 32 consecutive columns of a row: coalesced), then the 8 row-lanes are added
+// in order into part[chunk][c]; pass 2 adds the chunks in order.  With a row
+// weight w the sums are sum_r w[r] X[r, c], and column `cols` (one past the
+// last) is sum_r w[r] (the bias of the output layer).
+constexpr int kColRows = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(256) colsum_part(const T *X, const float *w, int rows, int cols, int with_ones,
+                                                   float *part)
 {
-    __shared__ float red[256];
-    const int c = blockIdx.x;
+    __shared__ float red[8][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int c = blockIdx.x * 32 + tx;
+    const int width = cols + with_ones;
+    const int r0 = blockIdx.y * kColRows, r1 = min(rows, r0 + kColRows);
     float s = 0.0f;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x)
-        s += dout[r] * (c < Hdim ? __bfloat162float(H[(size_t)r * Hdim + c]) : 1.0f);
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+    if (c < width) {
+        for (int r = r0 + ty; r < r1; r += 8) {
+            const float x = c < cols ? (float)X[(size_t)r * cols + c] : 1.0f;
+            s += w ? w[r] * x : x;
+        }
     }
-    if (threadIdx.x == 0) {
-        if (c < Hdim) gw[c] = red[0];
-        else gb[0] = red[0];
+    red[ty][tx] = s;
+    __syncthreads();
+    if (ty == 0 && c < width) {
+        float t = red[0][tx];
+        for (int y = 1; y < 8; ++y) t += red[y][tx];
+        part[(size_t)blockIdx.y * width + c] = t;
     }
 }
 
-// Column sums of a [rows x cols] FP32 matrix (bias gradients), fixed order.
-__global__ void column_sums(const float *X, int rows, int cols, float *out)
+__global__ void colsum_final(const float *part, int chunks, int width, float *out, float *out_extra)
 {
-    __shared__ float red[256];
-    const int c = blockIdx.x;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= width) return;
     float s = 0.0f;
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) s += X[(size_t)r * cols + c];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[c] = red[0];
+    for (int z = 0; z < chunks; ++z) s += part[(size_t)z * width + c];
+    if (out_extra && c == width - 1) out_extra[0] = s;
+    else out[c] = s;
 }
 
-// Sum of split-K partials in order: out[e] = sum_z part[z * count + e].
+// Transposed BF16 copies of weight matrices: dst[off + c rows + r] = src[off + r cols + c].
+struct TransposeJobs {
+    size_t off[6];
+    int rows[6], cols[6];
+    int count;
+};
+
+__global__ void transpose_bf16(const __nv_bfloat16 *src, __nv_bfloat16 *dst, TransposeJobs jobs)
+{
+    const int j = blockIdx.y;
+    if (j >= jobs.count) return;
+    const int rows = jobs.rows[j], cols = jobs.cols[j];
+    const size_t off = jobs.off[j];
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < (size_t)rows * cols; e += (size_t)gridDim.x * blockDim.x) {
+        const int r = (int)(e / cols), c = (int)(e % cols);
+        dst[off + (size_t)c * rows + r] = src[off + e];
+    }
+}
+
+// Sum of split-K partials in a fixed order: four running sums over the splits
+// z = 0, 4, 8, .. / 1, 5, .. / 2, .. / 3, .. (independent loads in flight),
+// then added as ((s0 + s1) + (s2 + s3)).
 __global__ void reduce_splits(const float *part, int splits, size_t count, float *out)
 {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= count) return;
-    float s = 0.0f;
-    for (int z = 0; z < splits; ++z) s += part[(size_t)z * count + e];
-    out[e] = s;
+    float s[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    int z = 0;
+    for (; z + 4 <= splits; z += 4) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] += part[(size_t)(z + u) * count + e];
+    }
+    for (int u = 0; z < splits; ++z, ++u) s[u] += part[(size_t)z * count + e];
+    out[e] = (s[0] + s[1]) + (s[2] + s[3]);
 }
 
 __global__ void adam(float *p, const float *g, float *m, float *v, __nv_bfloat16 *ph, size_t count,
@@ -382,17 +414,39 @@ int mlp_out_backward(const float *dout, const void *w, const float *Z, int rows,
     return (int)cudaGetLastError();
 }
 
-int mlp_out_weight_grad(const float *dout, const void *H, int rows, int Hdim, float *gw, float *gb,
+int mlp_colsum_chunks(int rows) { return (rows + kColRows - 1) / kColRows; }
+
+int mlp_out_weight_grad(const float *dout, const void *H, int rows, int Hdim, float *gw, float *gb, float *part,
                         cudaStream_t st)
 {
-    out_weight_grad<<<Hdim + 1, 256, 0, st>>>(dout, static_cast<const __nv_bfloat16 *>(H), rows, Hdim,
-                                              gw, gb);
+    const int width = Hdim + 1, chunks = mlp_colsum_chunks(rows);
+    colsum_part<__nv_bfloat16><<<dim3((width + 31) / 32, chunks), 256, 0, st>>>(
+        static_cast<const __nv_bfloat16 *>(H), dout, rows, Hdim, 1, part);
+    colsum_final<<<(width + 127) / 128, 128, 0, st>>>(part, chunks, width, gw, gb);
     return (int)cudaGetLastError();
 }
 
-int mlp_column_sums(const float *X, int rows, int cols, float *out, cudaStream_t st)
+int mlp_column_sums(const float *X, int rows, int cols, float *out, float *part, cudaStream_t st)
 {
-    column_sums<<<cols, 256, 0, st>>>(X, rows, cols, out);
+    const int chunks = mlp_colsum_chunks(rows);
+    colsum_part<float><<<dim3((cols + 31) / 32, chunks), 256, 0, st>>>(X, nullptr, rows, cols, 0, part);
+    colsum_final<<<(cols + 127) / 128, 128, 0, st>>>(part, chunks, cols, out, nullptr);
+    return (int)cudaGetLastError();
+}
+
+int mlp_transpose_weights(const void *src, void *dst, const size_t *off, const int *rows, const int *cols, int count,
+                          cudaStream_t st)
+{
+    if (count < 1 || count > 6) return (int)cudaErrorInvalidValue;
+    TransposeJobs jobs{};
+    for (int j = 0; j < count; ++j) {
+        jobs.off[j] = off[j];
+        jobs.rows[j] = rows[j];
+        jobs.cols[j] = cols[j];
+    }
+    jobs.count = count;
+    transpose_bf16<<<dim3(64, count), 256, 0, st>>>(static_cast<const __nv_bfloat16 *>(src),
+                                                    static_cast<__nv_bfloat16 *>(dst), jobs);
     return (int)cudaGetLastError();
 }
 

@@ -34,9 +34,15 @@ int mlp_vec_loss(float *out, const float *b, const float *y, const int *kr, int 
                  float *dout, void *douth, double *loss_part, double *cnt_part, cudaStream_t st);
 int mlp_out_backward(const float *dout, const void *w, const float *Z, int rows, int Hdim, float *dZ,
                      void *dZh, cudaStream_t st);
-int mlp_out_weight_grad(const float *dout, const void *H, int rows, int Hdim, float *gw, float *gb,
+// Column sums in two fixed-order passes through part[mlp_colsum_chunks(rows)][cols + 1].
+int mlp_colsum_chunks(int rows);
+int mlp_out_weight_grad(const float *dout, const void *H, int rows, int Hdim, float *gw, float *gb, float *part,
                         cudaStream_t st);
-int mlp_column_sums(const float *X, int rows, int cols, float *out, cudaStream_t st);
+int mlp_column_sums(const float *X, int rows, int cols, float *out, float *part, cudaStream_t st);
+// BF16 transposes of up to six weight matrices at the same flat offsets: dst
+// holds [cols][rows] where src holds [rows][cols].
+int mlp_transpose_weights(const void *src, void *dst, const size_t *off, const int *rows, const int *cols, int count,
+                          cudaStream_t st);
 int mlp_reduce_splits(const float *part, int splits, size_t count, float *out, cudaStream_t st);
 int mlp_adam(float *p, const float *g, float *m, float *v, void *ph, size_t count, float lr, float b1,
              float b2, float eps, int t, cudaStream_t st);

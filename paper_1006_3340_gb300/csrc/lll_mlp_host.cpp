@@ -41,6 +41,7 @@ struct MlpState {
     size_t off_wout = 0, off_bout = 0;
     float *d_p = nullptr, *d_g = nullptr, *d_m = nullptr, *d_v = nullptr;
     void *d_ph = nullptr; // BF16 copy of the parameters
+    void *d_phT = nullptr; // training: BF16 copies of the weight matrices transposed (same offsets)
     int adam_t = 0;
     bool trained = false;
     // work buffers, sized for `cap` rows
@@ -60,6 +61,7 @@ struct MlpState {
     void *d_douth = nullptr;        // head 1: bf16 [cap][outputs] dL/dout
     int *d_kr = nullptr;            // head 1: Euler step of each training row
     double *d_cnt = nullptr;        // head 1: per-block counts of live targets
+    float *d_colpart = nullptr;     // column-sum partials [chunks][width + 1]
 };
 
 void mlp_free_buffers(MlpState *m)
@@ -72,7 +74,8 @@ void mlp_free_buffers(MlpState *m)
     m->d_H.clear();
     m->d_Z.clear();
     for (int i = 0; i < 2; ++i) { cudaFree(m->d_dZ[i]); cudaFree(m->d_dZh[i]); m->d_dZ[i] = nullptr; m->d_dZh[i] = nullptr; }
-    cudaFree(m->d_split); cudaFree(m->d_loss);
+    cudaFree(m->d_split); cudaFree(m->d_loss); cudaFree(m->d_colpart);
+    m->d_colpart = nullptr;
     m->d_X = nullptr; m->d_Y = m->d_out = m->d_dout = nullptr; m->d_split = nullptr; m->d_loss = nullptr;
     m->cap = 0; m->split_cap = 0; m->loss_cap = 0;
 }
@@ -81,7 +84,7 @@ void mlp_free(MlpState *m)
 {
     if (!m) return;
     mlp_free_buffers(m);
-    cudaFree(m->d_p); cudaFree(m->d_g); cudaFree(m->d_m); cudaFree(m->d_v); cudaFree(m->d_ph);
+    cudaFree(m->d_p); cudaFree(m->d_g); cudaFree(m->d_m); cudaFree(m->d_v); cudaFree(m->d_ph); cudaFree(m->d_phT);
     cudaFree(m->d_acc);
     delete m;
 }
@@ -155,6 +158,8 @@ int ensure_rows(lll_ctx *ctx, MlpState *m, int rows)
     // loss partials: one per 8 rows (per-rate head), one per 128 outputs (vector head)
     const size_t lb = m->head ? ((size_t)rows * O + 127) / 128 : ((size_t)rows + 7) / 8;
     ok = ok && cudaMalloc((void **)&m->d_loss, sizeof(double) * lb) == cudaSuccess;
+    const size_t width = std::max<size_t>(std::max<size_t>(H, O), (size_t)m->in_pad) + 1;
+    ok = ok && cudaMalloc((void **)&m->d_colpart, sizeof(float) * width * mlp_colsum_chunks(rows)) == cudaSuccess;
     if (!ok) {
         mlp_free_buffers(m);
         return err(ctx, LLL_ENOMEM, "MLP work buffers");
@@ -215,8 +220,20 @@ int backward(lll_ctx *ctx, MlpState *m, int rows)
 {
     cudaStream_t st = ctx->stream;
     const char *ph = static_cast<const char *>(m->d_ph);
+    const char *phT = static_cast<const char *>(m->d_phT);
     const int H = m->hidden, L = m->layers;
-    const int splits_req = std::max(1, std::min(64, rows / 256));
+    // dW products: K = rows split into ranges of 64 rows (at most 128 CTAs), so
+    // that the 128 x din products fill the GPU
+    const int splits_req = std::max(1, std::min(128, rows / 64));
+    // transposed weights: the dX products then read K-contiguous rows
+    const bool tc = mlp_gemm_kind() == LLL_GEMM_TC;
+    if (tc) {
+        size_t off[6];
+        int rr[6], cc[6], cnt = 0;
+        for (int l = 1; l < L; ++l) { off[cnt] = m->offW[l]; rr[cnt] = H; cc[cnt] = H; ++cnt; }
+        if (m->head) { off[cnt] = m->off_wout; rr[cnt] = m->outputs; cc[cnt] = H; ++cnt; }
+        if (cnt > 0) MTRY(mlp_transpose_weights(m->d_ph, m->d_phT, off, rr, cc, cnt, st));
+    }
     if (m->head) {
         const int O = m->outputs;
         // dW_out = dout^T H_{L-1} (O x H), db_out = column sums, dZ_{L-1} = (dout W_out) * SiLU'(Z_{L-1})
@@ -226,11 +243,18 @@ int backward(lll_ctx *ctx, MlpState *m, int rows)
         MTRY(mlp_gemm(1, 0, 0, m->d_douth, O, m->d_H[L - 1], H, O, H, rows, splits_req, m->d_split, nullptr,
                       nullptr, nullptr, nullptr, st));
         MTRY(mlp_reduce_splits(m->d_split, splits, (size_t)O * H, m->d_g + m->off_wout, st));
-        MTRY(mlp_column_sums(m->d_dout, rows, O, m->d_g + m->off_bout, st));
-        MTRY(mlp_gemm(0, 0, 2, m->d_douth, O, ph + 2 * m->off_wout, H, rows, H, O, 1, nullptr, nullptr,
-                      m->d_Z[L - 1], m->d_dZ[0], m->d_dZh[0], st));
+        MTRY(mlp_column_sums(m->d_dout, rows, O, m->d_g + m->off_bout, m->d_colpart, st));
+        // dZ = (dout W_out) SiLU'(Z): B(k = o, n = h) from the transposed copy [H][O]
+        // (tcgen05), or read column-wise from W_out (mma.sync)
+        if (tc)
+            MTRY(mlp_gemm(0, 1, 2, m->d_douth, O, phT + 2 * m->off_wout, O, rows, H, O, 1, nullptr, nullptr,
+                          m->d_Z[L - 1], m->d_dZ[0], m->d_dZh[0], st));
+        else
+            MTRY(mlp_gemm(0, 0, 2, m->d_douth, O, ph + 2 * m->off_wout, H, rows, H, O, 1, nullptr, nullptr,
+                          m->d_Z[L - 1], m->d_dZ[0], m->d_dZh[0], st));
     } else {
-        MTRY(mlp_out_weight_grad(m->d_dout, m->d_H[L - 1], rows, H, m->d_g + m->off_wout, m->d_g + m->off_bout, st));
+        MTRY(mlp_out_weight_grad(m->d_dout, m->d_H[L - 1], rows, H, m->d_g + m->off_wout, m->d_g + m->off_bout,
+                                 m->d_colpart, st));
         MTRY(mlp_out_backward(m->d_dout, ph + 2 * m->off_wout, m->d_Z[L - 1], rows, H, m->d_dZ[0], m->d_dZh[0], st));
     }
     int cur = 0;
@@ -244,11 +268,16 @@ int backward(lll_ctx *ctx, MlpState *m, int rows)
         MTRY(mlp_gemm(1, 0, 0, m->d_dZh[cur], H, Hl, din, H, din, rows, splits_req, m->d_split, nullptr,
                       nullptr, nullptr, nullptr, st));
         MTRY(mlp_reduce_splits(m->d_split, splits, (size_t)H * din, m->d_g + m->offW[l], st));
-        MTRY(mlp_column_sums(m->d_dZ[cur], rows, H, m->d_g + m->offb[l], st));
+        MTRY(mlp_column_sums(m->d_dZ[cur], rows, H, m->d_g + m->offb[l], m->d_colpart, st));
         if (l > 0) {
-            // dZ_{l-1} = (dZ_l W_l) * SiLU'(Z_{l-1})
-            MTRY(mlp_gemm(0, 0, 2, m->d_dZh[cur], H, ph + 2 * m->offW[l], H, rows, H, H, 1, nullptr, nullptr,
-                          m->d_Z[l - 1], m->d_dZ[cur ^ 1], m->d_dZh[cur ^ 1], st));
+            // dZ_{l-1} = (dZ_l W_l) * SiLU'(Z_{l-1}), W_l read transposed ([in][out]) by the
+            // tcgen05 kernel, column-wise by the mma.sync kernel
+            if (tc)
+                MTRY(mlp_gemm(0, 1, 2, m->d_dZh[cur], H, phT + 2 * m->offW[l], H, rows, H, H, 1, nullptr, nullptr,
+                              m->d_Z[l - 1], m->d_dZ[cur ^ 1], m->d_dZh[cur ^ 1], st));
+            else
+                MTRY(mlp_gemm(0, 0, 2, m->d_dZh[cur], H, ph + 2 * m->offW[l], H, rows, H, H, 1, nullptr, nullptr,
+                              m->d_Z[l - 1], m->d_dZ[cur ^ 1], m->d_dZh[cur ^ 1], st));
             cur ^= 1;
         }
     }
@@ -321,7 +350,7 @@ int lll_mlp_init_head(lll_ctx *ctx, int hidden, int layers, int head, uint64_t s
     const size_t P = m->n_params;
     bool ok = cudaMalloc((void **)&m->d_p, 4 * P) == cudaSuccess && cudaMalloc((void **)&m->d_g, 4 * P) == cudaSuccess &&
               cudaMalloc((void **)&m->d_m, 4 * P) == cudaSuccess && cudaMalloc((void **)&m->d_v, 4 * P) == cudaSuccess &&
-              cudaMalloc(&m->d_ph, 2 * P) == cudaSuccess;
+              cudaMalloc(&m->d_ph, 2 * P) == cudaSuccess && cudaMalloc(&m->d_phT, 2 * P) == cudaSuccess;
     if (!ok) {
         mlp_free(m);
         return err(ctx, LLL_ENOMEM, "MLP parameters");
