@@ -311,9 +311,12 @@ void lll_batch_destroy(lll_batch *b);
  * Vector head (head = 1): one evaluation per (path, Euler step) gives every
  * rate's compensator: input (t s_t, u_0 .. u_{N-1}), outputs = n padded to 16
  * (column i - 1 for rate i; rates already fixed are ignored), trained on the
- * same records with the MSE over their live rates.  LLL_MLP then runs the
- * tcgen05 vector-head kernel (hidden 128, n <= 48) or, for other networks,
- * layer by layer (LLL_MLP_KERNEL_LAYERED), at about 1/n of the per-rate cost. */
+ * same records with the MSE over their live rates.  LLL_MLP then runs a
+ * tcgen05 vector-head kernel -- hidden 128 with n <= 48, or hidden 256 with
+ * n <= 121, input width <= 128 and at most 16 strikes (the whole simulation
+ * in one persistent launch, the weights streamed from L2) -- or, for other
+ * networks, layer by layer (LLL_MLP_KERNEL_LAYERED), at about 1/n of the
+ * per-rate cost. */
 typedef struct {
     int hidden;           /* width of every hidden layer: 128 or 256 */
     int layers;           /* hidden layers: 1..4 */
@@ -363,8 +366,9 @@ int lll_mlp_eval(lll_ctx *ctx, const float *x, const float *y, int rows, float *
  *     2..4 layers, where its shared-memory plan (weights, feature rows and
  *     the CTA's path state) fits: N <= 61 with 3 layers, N <= 66 with 2, and
  *     N <= 54 with 4 layers and 5 strikes (fewer with more strikes); the
- *     vector head needs n <= 48.  Its waits are bounded, and a wait that
- *     gives up makes the next read of the results return LLL_ETIMEOUT;
+ *     vector head needs n <= 48 with hidden 128, or hidden 256, 2..4 layers,
+ *     n <= 121 and at most 16 strikes.  Its waits are bounded, and a wait
+ *     that gives up makes the next read of the results return LLL_ETIMEOUT;
  *   LLL_MLP_KERNEL_LAYERED (3): any network (hidden 256, N up to 125): per
  *     Euler step, the rows (path, live rate) of a chunk of up to 2^20 rows go
  *     through the network layer by layer with the training GEMMs; AUTO takes

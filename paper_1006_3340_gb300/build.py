@@ -12,8 +12,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblll.so")
 
 SOURCES = ["lll_paths.cu", "lll_paths_group.cu", "lll_paths_tenor.cu", "lll_paths_step.cu", "lll_tables.cu", "lll_capi.cpp", "lll_quadrature.cpp", "lll_noalloc.cu",
-           "lll_mlp.cu", "lll_mlp_data.cu", "lll_mlp_host.cpp", "lll_mlp_path.cu", "lll_mlp_tc.cu", "lll_mlp_layered.cu", "lll_expand.cu", "lll_expand_host.cpp", "lll_batch.cpp", "lll_probe.cu", "lll_gemm_tc.cu"]
-HEADERS = ["lll_internal.h", "lll_device.cuh", "lll_ctx.h", "lll_mlp.h"]
+           "lll_mlp.cu", "lll_mlp_data.cu", "lll_mlp_host.cpp", "lll_mlp_path.cu", "lll_mlp_tc.cu", "lll_mlp_layered.cu", "lll_expand.cu", "lll_expand_host.cpp", "lll_batch.cpp", "lll_probe.cu", "lll_gemm_tc.cu", "lll_mlp_wide.cu"]
+HEADERS = ["lll_internal.h", "lll_device.cuh", "lll_ctx.h", "lll_mlp.h", "lll_tc.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include")]

@@ -685,6 +685,8 @@ EncodeTiledFn encode_tiled()
     return fn;
 }
 
+}  // namespace
+
 // Tensor map of a row-major BF16 matrix [rows x K] (leading dimension ld
 // elements, a multiple of 8) read in boxes of {64, box_rows} with the
 // 128-byte swizzle of the K-major operand layout.
@@ -700,6 +702,8 @@ bool make_tmap(CUtensorMap *tm, const void *base, int rows, int K, int ld, int b
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
+
+namespace {
 
 // Returns cudaErrorNotSupported (no launch) when the tensor map cannot be made;
 // the caller then uses the general kernel.

@@ -27,6 +27,10 @@ int mlp_gemm_tc(int ta, int tb, int epi, const void *A, int lda, const void *B, 
                 int splits, float *C, const float *bias, const float *Zin, float *Zout, void *Hout, int *err,
                 cudaStream_t st);
 int mlp_splits_used_tc(int K, int splits);
+// lll_gemm_tc.cu: a TMA tensor map (declared as void storage of 128 bytes, the
+// size of a CUtensorMap) of a row-major BF16 matrix [rows x K], leading
+// dimension ld (a multiple of 8), boxes {64, box_rows}, 128-byte swizzle.
+bool make_tmap(struct CUtensorMap_st *tm, const void *base, int rows, int K, int ld, int box_rows);
 
 int mlp_out_loss(const void *H, int Hdim, const void *w, const float *b, const float *y, int rows,
                  float *out, float *dout, double *loss_part, cudaStream_t st);
@@ -100,5 +104,13 @@ bool mlp_tc_vec_supported(int hidden, int layers, int in_pad, int outputs, int n
 int mlp_tc_vec_occupancy(int layers, int in_pad, size_t smem, int *blocks_per_sm);
 int launch_mlp_tc_vec(int layers, int in_pad, int grid, size_t smem, cudaStream_t st, const PathArgs &a,
                       const MlpArgs &g);
+
+// lll_mlp_wide.cu (tcgen05, vector head of width 256: the whole simulation in
+// one persistent kernel, one 128-path tile per CTA at a time, weights streamed
+// by TMA; acc: [grid][n][ns][4] FP64 Kahan sums, zeroed by the caller)
+size_t mlp_wide_smem(int n, int ns);
+bool mlp_wide_supported(int hidden, int layers, int in_pad, int outputs, int n, int ns, int product);
+int launch_mlp_wide(int layers, int in_pad, int outputs, int grid, cudaStream_t st, const PathArgs &a,
+                    const MlpArgs &g, double *acc);
 
 }  // namespace lll

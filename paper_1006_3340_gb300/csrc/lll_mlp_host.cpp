@@ -655,6 +655,74 @@ int simulate_mlp_layered(lll_ctx *ctx, MlpState *m, uint64_t first_path, uint64_
     return LLL_OK;
 }
 
+// LLL_MLP with a 256-wide vector-head network (lll_mlp_wide.cu): one
+// persistent launch, a CTA per SM, 128-path tiles; the CTAs' FP64 Kahan sums
+// go to the partials and the fixed-order final reduction.
+int simulate_mlp_wide(lll_ctx *ctx, MlpState *m, uint64_t first_path, uint64_t paths, uint64_t seed)
+{
+    LaunchPlan plan;
+    int rc = plan_launch(ctx, LLL_FULL, first_path, paths, seed, &plan, false);
+    if (rc != LLL_OK) return rc;
+    const uint64_t tiles = (paths + 127) / 128;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(tiles, (uint64_t)ctx->sm_count));
+    const size_t cells = (size_t)grid * ctx->n * ctx->ns;
+    if (4 * cells > m->acc_cap) {
+        cudaFree(m->d_acc);
+        m->d_acc = nullptr;
+        m->acc_cap = 0;
+        if (cudaMalloc((void **)&m->d_acc, 8 * 4 * cells) != cudaSuccess) return err(ctx, LLL_ENOMEM, "accumulators");
+        m->acc_cap = 4 * cells;
+    }
+    const size_t nout = (size_t)plan.n_out;
+    if ((size_t)grid * nout > ctx->partials_cap) {
+        cudaFree(ctx->d_partials);
+        ctx->d_partials = nullptr;
+        ctx->partials_cap = 0;
+        if (cudaMalloc((void **)&ctx->d_partials, 8 * grid * nout) != cudaSuccess) return err(ctx, LLL_ENOMEM, "partials");
+        ctx->partials_cap = (size_t)grid * nout;
+    }
+    if (nout > ctx->sums_cap) {
+        cudaFree(ctx->d_sums);
+        ctx->d_sums = nullptr;
+        ctx->sums_cap = 0;
+        if (cudaMalloc((void **)&ctx->d_sums, 8 * nout) != cudaSuccess) return err(ctx, LLL_ENOMEM, "sums");
+        ctx->sums_cap = nout;
+    }
+    if (!ctx->d_err && cudaMalloc((void **)&ctx->d_err, sizeof(int)) != cudaSuccess)
+        return err(ctx, LLL_ENOMEM, "error word");
+    PathArgs a = plan.args;
+    a.partials = ctx->d_partials;
+    a.snap = ctx->d_snap; a.snap_stride = ctx->snap_stride; a.snap_pitch = ctx->n_snap;
+    a.n_snap = ctx->d_snap ? std::min<uint64_t>(ctx->n_snap, (paths + ctx->snap_stride - 1) / ctx->snap_stride) : 0;
+    MlpArgs g{};
+    g.wh = static_cast<const __nv_bfloat16 *>(m->d_ph);
+    g.wp = m->d_p;
+    for (int l = 0; l < m->layers; ++l) { g.offW[l] = m->offW[l]; g.offb[l] = m->offb[l]; }
+    g.off_wout = m->off_wout;
+    g.off_bout = m->off_bout;
+    g.sc = m->sc;
+    g.Ctab = ctx->d_C;
+    g.in_pad = m->in_pad;
+    g.err = ctx->d_err;
+    g.stall_mma = ctx->inject == LLL_INJECT_MMA_STALL ? 1 : 0;
+    ctx->inject = LLL_INJECT_NONE; // one launch only
+    cudaStream_t st = ctx->stream;
+    MTRY(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+    MTRY(cudaMemsetAsync(m->d_acc, 0, 8 * 4 * cells, st));
+    MTRY(cudaEventRecord(ctx->ev[0], st));
+    MTRY(launch_mlp_wide(m->layers, m->in_pad, m->outputs, grid, st, a, g, m->d_acc));
+    MTRY(cudaEventRecord(ctx->ev[1], st));
+    MTRY(launch_mlp_acc_to_partials(m->d_acc, cells, ctx->d_partials, st));
+    MTRY(launch_finalize(ctx->d_partials, grid, (int)nout, ctx->d_sums, st));
+    MTRY(cudaEventRecord(ctx->ev[2], st));
+    ctx->simulated = true;
+    ctx->err_pending = true;
+    ctx->gemm_err_pending = false;
+    ctx->last_paths = paths;
+    ctx->last_snap_paths = a.n_snap;
+    return LLL_OK;
+}
+
 // lll_simulate(LLL_MLP): the full scheme with the network's compensator.
 int simulate_mlp(lll_ctx *ctx, uint64_t first_path, uint64_t paths, uint64_t seed)
 {
@@ -664,12 +732,14 @@ int simulate_mlp(lll_ctx *ctx, uint64_t first_path, uint64_t paths, uint64_t see
     if (m->head) {
         vec_tc = mlp_tc_vec_supported(m->hidden, m->layers, m->in_pad, m->outputs, ctx->n) &&
                  mlp_tc_vec_smem(m->layers, m->in_pad, ctx->n, ctx->ns) <= 227 * 1024;
+        const bool wide = mlp_wide_supported(m->hidden, m->layers, m->in_pad, m->outputs, ctx->n, ctx->ns, ctx->product);
         if (ctx->mlp_kernel == LLL_MLP_KERNEL_WARP)
             return err(ctx, LLL_EUNSUPPORTED, "the mma.sync kernel has no vector head");
-        if (ctx->mlp_kernel == LLL_MLP_KERNEL_TC && !vec_tc)
-            return err(ctx, LLL_EUNSUPPORTED, "the tcgen05 vector-head kernel does not support this network");
-        if (ctx->mlp_kernel == LLL_MLP_KERNEL_LAYERED || !vec_tc)
+        if (ctx->mlp_kernel == LLL_MLP_KERNEL_TC && !vec_tc && !wide)
+            return err(ctx, LLL_EUNSUPPORTED, "the tcgen05 vector-head kernels do not support this network");
+        if (ctx->mlp_kernel == LLL_MLP_KERNEL_LAYERED || (!vec_tc && !wide))
             return simulate_mlp_layered(ctx, m, first_path, paths, seed);
+        if (!vec_tc) return simulate_mlp_wide(ctx, m, first_path, paths, seed);
     }
     const size_t smem_tc = vec_tc ? mlp_tc_vec_smem(m->layers, m->in_pad, ctx->n, ctx->ns)
                                   : mlp_tc_smem(m->layers, m->in_pad, ctx->n, ctx->ns);
