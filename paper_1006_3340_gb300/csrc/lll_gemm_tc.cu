@@ -39,6 +39,7 @@
 #include "../../include/lll.h"
 #include "lll_internal.h"
 #include "lll_mlp.h"
+#include "lll_tc.cuh"
 
 namespace lll {
 namespace {
@@ -46,7 +47,6 @@ namespace {
 constexpr int kM = 128;                      // rows per CTA tile (TMEM lanes)
 constexpr int kWsMinRows = 8192;             // streamed rows from which the weight-stationary kernel is used
 constexpr int kThreadsG = 128;
-constexpr long long kWaitBudgetG = 4000000000ll; // clock cycles (about 2 s)
 
 struct GemmArgs {
     const __nv_bfloat16 *A;
@@ -60,26 +60,10 @@ struct GemmArgs {
     int *err;
 };
 
-__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// K-major, 128-byte swizzle, 8-row groups 1024 B apart (rows of 64 BF16).
-__device__ __forceinline__ uint64_t sdesc(uint32_t a)
-{
-    return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
+using namespace tc;
 
 // D FP32, A and B BF16, both K-major, M = 128, N = n.
-__host__ __device__ constexpr uint32_t idesc(int n)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kM >> 4) << 24);
-}
-
-// Byte offset of 16-byte chunk c8 (8 consecutive K) of row r in a 64-wide K block.
-__device__ __forceinline__ uint32_t swz(int r, int c8)
-{
-    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c8 ^ (r & 7)) << 4));
-}
+__host__ __device__ constexpr uint32_t idesc(int n) { return idesc_m128(n); }
 
 __device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, int bytes)
 {
@@ -88,11 +72,6 @@ __device__ __forceinline__ void cp_async16_zfill(uint32_t dst, const void *src, 
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
-}
 
 // Bounded wait for phase parity `par` of barrier b; false when it gave up
 // (then the launch's error word is set).  Only thread 0 of a CTA waits; the
@@ -110,46 +89,20 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *b, uint32_t par, int
                      : "r"(a), "r"(par)
                      : "memory");
         if (ok) return true;
-        if (clock64() - t0 > kWaitBudgetG) {
+        if (clock64() - t0 > kWaitBudget) {
             atomicOr(err, 1);
             return false;
         }
     }
 }
 
-__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void mma_ss(uint32_t d, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc)
+// 16 accumulator columns of this thread's TMEM lane, waited for.
+__device__ __forceinline__ void tmem_ld16_wait(uint32_t ta, uint32_t (&r)[16])
 {
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                 "l"(ad), "l"(bd), "r"(id), "r"(acc));
+    tmem_ld16(ta, r);
+    tmem_wait(r);
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t *b)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(b))
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&r)[16])
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-                 "tcgen05.wait::ld.sync.aligned;"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                   "=r"(r[14]), "=r"(r[15])
-                 : "r"(ta)
-                 : "memory");
-}
-
-__device__ __forceinline__ float tanh_approx(float x)
-{
-    float y;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 __device__ __forceinline__ float silu(float z) { return 0.5f * z * (1.0f + tanh_approx(0.5f * z)); }
 __device__ __forceinline__ float silu_grad(float z)
 {
@@ -309,7 +262,7 @@ __global__ void __launch_bounds__(kThreadsG) gemm_tc(const GemmArgs g)
             for (int c16 = 0; c16 < CG; c16 += 16) {
                 uint32_t r[16];
                 if (nkb > 0) {
-                    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + cg0 + c16, r);
+                    tmem_ld16_wait(tmem + ((uint32_t)(warp * 32) << 16) + cg0 + c16, r);
                 } else {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) r[j] = 0u;
@@ -445,32 +398,6 @@ struct WsShape {
     static constexpr int STG = SA ? 2 : 3;     // ring stages (64 / 48 KB)
 };
 
-__device__ __forceinline__ bool ws_wait(uint64_t *b, uint32_t par, volatile int *abort, int *err)
-{
-    const uint32_t a = saddr(b);
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t ok;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     " selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(ok)
-                     : "r"(a), "r"(par)
-                     : "memory");
-        if (ok) return true;
-        if (*abort) return false;
-        if (clock64() - t0 > kWaitBudgetG) {
-            *abort = 1;
-            atomicOr(err, 1);
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *b)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
-}
-
 template <int SA, int EPI, int NT>
 __global__ void __launch_bounds__(kWsThreads, 1) gemm_ws(const GemmArgs g, const __grid_constant__ CUtensorMap tmap)
 {
@@ -529,7 +456,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) gemm_ws(const GemmArgs g, const
             for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
                 for (int kb = 0; kb < KB; ++kb, ++it) {
                     const int s = it % S::STG, u = it / S::STG;
-                    if (u >= 1 && !(ok = ws_wait(&empty[s], (u - 1) & 1, abort, g.err))) break;
+                    if (u >= 1 && !(ok = mbar_wait(&empty[s], (u - 1) & 1, abort, g.err))) break;
                     const uint32_t bar = saddr(&full[s]);
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
                                  "r"(S::KBLK)
@@ -553,12 +480,12 @@ __global__ void __launch_bounds__(kWsThreads, 1) gemm_ws(const GemmArgs g, const
             bool ok = true;
             for (int t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++j) {
                 const int b = j & 1, v = j >> 1;
-                if (v >= 1 && !(ok = ws_wait(&acce[b], (v - 1) & 1, abort, g.err))) break;
+                if (v >= 1 && !(ok = mbar_wait(&acce[b], (v - 1) & 1, abort, g.err))) break;
                 tc_after();
                 const uint32_t d = tmem + b * MN;
                 for (int kb = 0; kb < KB; ++kb, ++it) {
                     const int s = it % S::STG, u = it / S::STG;
-                    if (!(ok = ws_wait(&full[s], u & 1, abort, g.err))) break;
+                    if (!(ok = mbar_wait(&full[s], u & 1, abort, g.err))) break;
                     tc_after();
                     const uint32_t rb = sring + s * S::KBLK, sb = sst + kb * SBLK;
 #pragma unroll
@@ -572,7 +499,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) gemm_ws(const GemmArgs g, const
             }
             // every product issued by this lane has completed once this arrives
             mma_commit(&fin);
-            ws_wait(&fin, 0, abort, g.err);
+            mbar_wait(&fin, 0, abort, g.err);
         }
         __syncwarp();
     } else {
@@ -585,7 +512,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) gemm_ws(const GemmArgs g, const
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++j) {
             const int b = j & 1, v = j >> 1;
             bool ok = true;
-            if (lane == 0) ok = ws_wait(&accf[b], v & 1, abort, g.err);
+            if (lane == 0) ok = mbar_wait(&accf[b], v & 1, abort, g.err);
             if (!__shfl_sync(0xffffffffu, ok, 0)) break;
             tc_after();
             const int r0 = (SA ? 0 : t * kM) + q * 32, c0 = SA ? t * S::TR : 0;
@@ -593,8 +520,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) gemm_ws(const GemmArgs g, const
             const int m = r0 + lane; // this thread's accumulator row
             for (int cg = half * (MN / 2); cg < (half + 1) * (MN / 2) && cg < cols; cg += 32) {
                 uint32_t r[2][16];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + b * MN + cg, r[0]);
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + b * MN + cg + 16, r[1]);
+                tmem_ld16_wait(tmem + ((uint32_t)(q * 32) << 16) + b * MN + cg, r[0]);
+                tmem_ld16_wait(tmem + ((uint32_t)(q * 32) << 16) + b * MN + cg + 16, r[1]);
                 float f[32];
 #pragma unroll
                 for (int c = 0; c < 32; ++c) {

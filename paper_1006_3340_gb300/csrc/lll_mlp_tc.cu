@@ -39,6 +39,7 @@
 #include "lll_device.cuh"
 #include "lll_internal.h"
 #include "lll_mlp.h"
+#include "lll_tc.cuh"
 
 namespace lll {
 namespace {
@@ -49,190 +50,19 @@ constexpr int kGroups = 2;            // path tiles in flight per CTA
 constexpr int kEpiWarps = 8 * kGroups; // 4 TMEM lane quadrants x 4 column quarters (vector head: x 2 halves x 2 tiles)
 constexpr int kThreads = (kEpiWarps + 1) * 32;
 constexpr int kTileBytes = kRows * 128; // one 64-wide K block of a 128-row operand
-constexpr long long kWaitBudget = 4000000000ll; // clock cycles (about 2 s)
+using namespace tc;
 
-__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sdesc(uint32_t a)
-{
-    return (uint64_t)((a >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
-           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
-}
-
-// Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = n.
-__host__ __device__ constexpr uint32_t idesc_n(int n)
-{
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
-// Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = kH.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kH >> 3) << 17) |
-                            ((uint32_t)(kRows >> 4) << 24);
+// Instruction descriptor of the hidden layers: D FP32, A and B BF16, both K-major, M = 128, N = kH.
+constexpr uint32_t kIdesc = idesc_m128(kH);
+__host__ __device__ constexpr uint32_t idesc_n(int n) { return idesc_m128(n); }
 
 // Byte offset of the 16-byte chunk c8 (0..7) of K block kb in row r of a 128-row operand.
-__device__ __forceinline__ uint32_t chunk_off(int r, int kb, int c8)
-{
-    return (uint32_t)(kb * kTileBytes + (r >> 3) * 1024 + (r & 7) * 128 + ((c8 ^ (r & 7)) << 4));
-}
+__device__ __forceinline__ uint32_t chunk_off(int r, int kb, int c8) { return (uint32_t)(kb * kTileBytes) + swz(r, c8); }
 
 __device__ __forceinline__ float bf16_round(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-__device__ __forceinline__ uint32_t pack2(float lo, float hi)
-{
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<const uint32_t *>(&v);
-}
-
-__device__ __forceinline__ float tanh_approx(float x)
-{
-    float y;
-    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(saddr(b)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *b)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(b)) : "memory");
-}
-
-// Wait for the completion of the phase of parity `par`.  Gives up when the
-// CTA's abort word is set or after kWaitBudget cycles (then sets it, and the
-// launch's error word).
-__device__ __forceinline__ uint32_t mbar_test(uint32_t a, uint32_t par)
-{
-    uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                 " selp.u32 %0, 1, 0, p;\n}\n"
-                 : "=r"(ok)
-                 : "r"(a), "r"(par)
-                 : "memory");
-    return ok;
-}
-
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t par, volatile int *abort, int *err)
-{
-    const uint32_t a = saddr(b);
-    if (mbar_test(a, par)) return true; // completed already: no clock read, no suspend
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t ok;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     " selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(ok)
-                     : "r"(a), "r"(par)
-                     : "memory");
-        if (ok) return true;
-        if (*abort) return false;
-        if (clock64() - t0 > kWaitBudget) {
-            *abort = 1;
-            atomicOr(err, 1);
-            return false;
-        }
-    }
-}
-
-// The same for a whole warp: every lane tests the barrier and the decisions
-// (done, give up) are warp-uniform, so the warp stays converged and all lanes
-// leave a loop together before any .sync.aligned tcgen05 instruction.
-__device__ __forceinline__ bool warp_wait(uint64_t *b, uint32_t par, volatile int *abort, int *err)
-{
-    const uint32_t a = saddr(b);
-    if (__all_sync(0xffffffffu, mbar_test(a, par))) return true;
-    const long long t0 = clock64();
-    while (true) {
-        uint32_t ok;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     " selp.u32 %0, 1, 0, p;\n}\n"
-                     : "=r"(ok)
-                     : "r"(a), "r"(par)
-                     : "memory");
-        if (__all_sync(0xffffffffu, ok)) return true;
-        const bool stop = *abort || clock64() - t0 > kWaitBudget;
-        if (__any_sync(0xffffffffu, stop)) {
-            if ((threadIdx.x & 31) == 0 && !*abort) {
-                *abort = 1;
-                atomicOr(err, 1);
-            }
-            return false;
-        }
-    }
-}
-
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t acc)
-{
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                 "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
-}
-
-__device__ __forceinline__ void mma_bf16_id(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
-{
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-}
-
-// A operand in tensor memory: 128 lanes (rows) x 8 columns, each column two
-// BF16 values of consecutive K (lower K in the low half).
-__device__ __forceinline__ void mma_bf16_ts(uint32_t d, uint32_t at, uint64_t bd, uint32_t acc)
-{
-    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                 " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
-                 "r"(at), "l"(bd), "r"(kIdesc), "r"(acc));
-}
-
-__device__ __forceinline__ void tmem_st8(uint32_t ta, const uint32_t (&r)[8])
-{
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta), "r"(r[0]),
-                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
-                 : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void mma_commit(uint64_t *b)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(b))
-                 : "memory");
-}
-
-// 16 consecutive FP32 accumulator columns of this thread's TMEM lane: the
-// load is issued by tmem_ld16 and its registers become valid at tmem_wait16,
-// which takes them as in/out operands so that no use is scheduled before it.
-#define LLL_R16(r) "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), \
-    "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
-
-__device__ __forceinline__ void tmem_ld16(uint32_t ta, uint32_t (&r)[16])
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                   "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                   "=r"(r[14]), "=r"(r[15])
-                 : "r"(ta));
-}
-
-// 8 consecutive columns into r[0..7] (completed by tmem_wait16 on the enclosing array)
-__device__ __forceinline__ void tmem_ld8(uint32_t ta, uint32_t *r)
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(ta));
-}
-
-__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16])
-{
-    asm volatile("tcgen05.wait::ld.sync.aligned;" : LLL_R16(r) : : "memory");
-}
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t acc) { mma_ss(d, ad, bd, kIdesc, acc); }
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d, uint32_t at, uint64_t bd, uint32_t acc) { mma_ts(d, at, bd, kIdesc, acc); }
 
 // Bias + SiLU of 8 accumulator values: with z = v + b and hz = z / 2 (from
 // the half bias hb), SiLU(z) = z sigma(z) = hz + hz tanh(hz), the same
@@ -253,21 +83,6 @@ __device__ __forceinline__ void silu8(const uint32_t *v, const float *hb, float 
         sv[e] = r.x;
         sv[e + 1] = r.y;
     }
-}
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ void kahan_add(double *s, double *c, double x)
-{
-    const double y = x - *c;
-    const double t = *s + y;
-    *c = (t - *s) - y;
-    *s = t;
 }
 
 // Shared-memory plan; operand tiles first (1024-byte aligned).
@@ -545,7 +360,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                             float o4[4] = {0.0f, 0.0f, 0.0f, 0.0f};
                             uint32_t ra[16], rb[16];
                             tmem_ld16(dbuf, ra);
-                            tmem_wait16(ra);
+                            tmem_wait(ra);
                             tmem_ld16(dbuf + 16, rb);
 #pragma unroll
                             for (int cc = 0; cc < 2; ++cc) {
@@ -574,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                                 }
                                 // activations K = 32 cq + 16 cc .. +15 of this row: 8 packed TMEM columns
                                 if (l < L - 1) tmem_st8(aq + gi * (kH / 2) + cc * 8, pk);
-                                if (cc == 0) tmem_wait16(rb);
+                                if (cc == 0) tmem_wait(rb);
                             }
                             if (l < L - 1) {
                                 tmem_wait_st();
@@ -927,7 +742,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
                         const float *hbl = bias + l * kH + cq * 32;
                         uint32_t ra[16], rb[16];
                         tmem_ld16(dbuf, ra);
-                        tmem_wait16(ra);
+                        tmem_wait(ra);
                         tmem_ld16(dbuf + 16, rb);
 #pragma unroll
                         for (int cc = 0; cc < 2; ++cc) {
@@ -941,7 +756,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
                                 for (int e = 0; e < 4; ++e) pk[qd * 4 + e] = pack2(sv[2 * e], sv[2 * e + 1]);
                             }
                             tmem_st8(dq + 2 * kH + gi * (kH / 2) + cq * 16 + cc * 8, pk);
-                            if (cc == 0) tmem_wait16(rb);
+                            if (cc == 0) tmem_wait(rb);
                         }
                         tmem_wait_st();
                         tc_before();
@@ -966,7 +781,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
                     uint32_t ro[16];
                     tmem_ld8(dq + gi * kH + 8 * cq, ro);
                     tmem_ld8(dq + gi * kH + 8 * cq + 32, ro + 8);
-                    tmem_wait16(ro);
+                    tmem_wait(ro);
                     const uint64_t lp = lp0 + gi * kRows;
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {

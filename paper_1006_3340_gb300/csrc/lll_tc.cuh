@@ -140,6 +140,25 @@ __device__ __forceinline__ void mma_ss(uint32_t d, uint64_t ad, uint64_t bd, uin
                  "l"(ad), "l"(bd), "r"(id), "r"(acc));
 }
 
+// The same with A in tensor memory: at addresses 128 lanes (rows) x 8 columns,
+// each column two BF16 values of consecutive K (lower K in the low half).
+__device__ __forceinline__ void mma_ts(uint32_t d, uint32_t at, uint64_t bd, uint32_t id, uint32_t acc)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+                 "r"(at), "l"(bd), "r"(id), "r"(acc));
+}
+
+// 8 columns of this thread's TMEM lane from r[0..7]; complete at tmem_wait_st.
+__device__ __forceinline__ void tmem_st8(uint32_t ta, const uint32_t *r)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(ta), "r"(r[0]),
+                 "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Arrive on b once every product issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t *b)
 {
