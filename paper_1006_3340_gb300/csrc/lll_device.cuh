@@ -105,6 +105,44 @@ __device__ __forceinline__ void maturity_products(const PathArgs &a, int m, ZF z
     Lm = expf(z(m));
 }
 
+// The same quantities, with the factors (1 + delta L_i) of eight rates at a
+// time computed ahead of their place in the sequential product: the same
+// operations in the same order (a factor past m is 1, an exact product), so
+// the results are identical, while the loads and exponentials of a group
+// overlap instead of forming one dependent chain.
+template <class ZF>
+__device__ __forceinline__ void maturity_products_grouped(const PathArgs &a, int m, ZF z, double &P, double &S,
+                                                          float &Lm)
+{
+    if (a.product == 0) {
+        float Pf = 1.0f;
+        for (int i0 = a.n; i0 > m; i0 -= 8) {
+            float f[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) f[u] = i0 - u > m ? fmaf(a.delta, expf(z(i0 - u)), 1.0f) : 1.0f;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) Pf *= f[u];
+        }
+        P = (double)Pf;
+        S = 1.0;
+    } else {
+        P = 1.0;
+        S = 1.0;
+        for (int i0 = a.n; i0 > m; i0 -= 8) {
+            double f[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) f[u] = i0 - u > m ? 1.0 + (double)(a.delta * expf(z(i0 - u))) : 1.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 - u > m) {
+                    P *= f[u];
+                    S += P;
+                }
+        }
+    }
+    Lm = expf(z(m));
+}
+
 // Discounted payoff (under the terminal measure, times B(0, T_N)) at T_m for
 // strike K.  Caplet, Eq. (caplet): delta B(0,T_N) prod_{l>m} (1 + delta L_l) (L_m - K)^+.
 // Co-terminal payer swaption on the swap over [T_m, T_N]: its value at T_m is

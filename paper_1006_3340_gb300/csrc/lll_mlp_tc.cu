@@ -826,8 +826,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
                     float Lm[kGroups];
 #pragma unroll
                     for (int gi = 0; gi < kGroups; ++gi)
-                        maturity_products(a, m, [&](int i) { return st[(size_t)(i - 1) * T + gi * kRows] + a.Z0[i - 1]; },
-                                          Pp[gi], Sp[gi], Lm[gi]);
+                        maturity_products_grouped(a, m, [&](int i) { return st[(size_t)(i - 1) * T + gi * kRows] + __ldg(a.Z0 + i - 1); },
+                                                  Pp[gi], Sp[gi], Lm[gi]);
                     for (int qs = 0; qs < ns; ++qs) {
                         const float K = a.strikes[(size_t)(m - 1) * ns + qs];
                         double s1 = 0.0, s2 = 0.0;

@@ -120,48 +120,6 @@ __device__ __forceinline__ void silu16(const uint32_t *v, const float4 (&b4)[4],
     }
 }
 
-// The maturity products of maturity_products (lll_device.cuh) from the state
-// rows st[(i - 1) kRowsW]: the same operations in the same order, with the
-// factors (1 + delta L_i) of eight rates computed ahead of their place in the
-// sequential product, so that their loads and exponentials overlap.
-__device__ __forceinline__ void products_ahead(const PathArgs &a, int m, const float *st, double &P, double &S,
-                                               float &Lm)
-{
-    if (a.product == 0) {
-        float Pf = 1.0f;
-        for (int i0 = a.n; i0 > m; i0 -= 8) {
-            float f[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int i = i0 - u;
-                f[u] = i > m ? fmaf(a.delta, expf(st[(i - 1) * kRowsW] + __ldg(a.Z0 + i - 1)), 1.0f) : 1.0f;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) Pf *= f[u]; // factors past m are 1: exact
-        }
-        P = (double)Pf;
-        S = 1.0;
-    } else {
-        P = 1.0;
-        S = 1.0;
-        for (int i0 = a.n; i0 > m; i0 -= 8) {
-            double f[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int i = i0 - u;
-                f[u] = i > m ? 1.0 + (double)(a.delta * expf(st[(i - 1) * kRowsW] + __ldg(a.Z0 + i - 1))) : 1.0;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (i0 - u > m) {
-                    P *= f[u];
-                    S += P;
-                }
-        }
-    }
-    Lm = expf(st[(m - 1) * kRowsW] + __ldg(a.Z0 + m - 1));
-}
-
 template <int L, int KB0>
 __global__ void __launch_bounds__(kThreadsW, 1)
     mlp_wide_kernel(const PathArgs a, const MlpArgs g, const __grid_constant__ WideMaps maps, double *acc)
@@ -480,7 +438,8 @@ __global__ void __launch_bounds__(kThreadsW, 1)
                             for (int w = 1; w < 4; ++w) Pf *= mpart[w * kRowsW + row];
                             Lm = mpart[4 * kRowsW + row];
                         } else {
-                            products_ahead(a, m, st, Pp, Sp, Lm);
+                            maturity_products_grouped(
+                                a, m, [&](int i) { return st[(i - 1) * kRowsW] + __ldg(a.Z0 + i - 1); }, Pp, Sp, Lm);
                         }
                         // per-path payoffs are FP32 values (caplets) or FP64 (swaptions);
                         // the warp's sums over its 32 paths are formed in FP32, whose
