@@ -21,7 +21,8 @@ most T_N years (the per-rate and N = 40 vector-head tests use the same bound).
 * failure detection without a GPU fault: with the MMA lane stalled, the
   bounded waits give up, the results read back as LLL_ETIMEOUT and the next
   simulation on the same context is bit for bit the reference;
-* co-terminal swaptions against the swaption prices of the oracle's paths.
+* co-terminal swaptions against the swaption prices of the oracle's paths;
+* the two- and three-layer instantiations with a one-K-block input (N = 10).
 """
 import numpy as np
 import pytest
@@ -183,3 +184,37 @@ def test_wide_kernel_swaptions_match_fp64_scheme(lll, wide):
     tol = 3.0 * 0.25 * _tol(wl, scales)
     assert np.abs(p - want).max() <= tol, (np.abs(p - want).max(), tol)
     assert np.abs(p - p_l).max() <= tol
+
+
+@pytest.mark.parametrize("layers", [2, 3])
+def test_wide_kernel_small_network_variants_match_fp64(lll, layers):
+    """The other instantiations of the fused kernel: two and three hidden
+    layers of 256 and an input of one 64-wide K block (N = 10: input 11 padded
+    to 16), over two full tiles and a ragged third, path by path against the
+    FP64 oracle (same bound as above)."""
+    wl = workloads.small_plain(paths=2 * 128 + 37)
+    x, W = quadrature.rule_for(wl)
+    sim = lll.LevyLibor(wl, x, W)
+    try:
+        lll.lll_mlp_init_head(sim.ctx, H, layers, 1, seed=11 + layers)
+        n_params, in_dim, in_pad, offs = lll.lll_mlp_layout(sim.ctx, layers)
+        head, outputs = lll.lll_mlp_shape(sim.ctx)
+        assert in_pad <= 64
+        flat, scales = lll.lll_mlp_params(sim.ctx, 0, count=n_params)
+        scales = np.array(scales, dtype=np.float32)
+        scales[4] = 1e-3
+        lll.lll_mlp_params(sim.ctx, 1, flat, scales=scales)
+        cnt = wl.paths
+        sim.simulate("mlp", paths=cnt, snapshots=cnt)
+        z = sim.paths(0, cnt).astype(np.float64)
+        p, _ = sim.prices()
+    finally:
+        sim.close()
+    params = omlp.params_from_flat(flat, offs, layers, H, in_dim, in_pad, outputs=outputs)
+    ref = omlp.simulate_scheme(ora.OracleModel(wl, x, W), params, scales, npaths=cnt, head=1)
+    mask = ~np.isnan(ref["snap"])
+    assert np.array_equal(mask, ~np.isnan(z))
+    tol = _tol(wl, scales)
+    per_path = np.nanmax(np.abs(z - ref["snap"]).reshape(cnt, -1), axis=1)
+    assert np.all(per_path <= tol), (per_path.max(), tol)
+    assert np.abs(p - ref["price"]).max() <= 1e-2 * tol
