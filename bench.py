@@ -276,7 +276,9 @@ def run_batch(args, steps, warmup, with_cpu=True, with_e2e=True, rates=None):
     dev = torch.device("cuda", 0)
     from paper_1006_3340_gb300 import autotune, lll
 
-    wls = workloads.batched_instances()
+    # --paths: the batch's total path budget (default 2^24; smaller totals are
+    # for profiling captures, the instances' budgets scale along)
+    wls = workloads.batched_instances(total_paths=(args.paths if args.workload == "batch256" else 0) or (1 << 24))
     schemes = [s for s in args.schemes.split(",") if s in ("picard", "full")] or ["picard", "full"]
     inst = []
     for wl in wls:
@@ -286,7 +288,15 @@ def run_batch(args, steps, warmup, with_cpu=True, with_e2e=True, rates=None):
     lane_ops = sum(wl.paths * wl.units_per_path() * 3 * wl.Q for wl in wls)
     caplets = sum(wl.n * wl.strikes.shape[1] for wl in wls)
     b, keep = lll.lll_batch_init(inst)  # default stream, the one torch's events record on
-    tuned = autotune.tune_batch(b, inst, "full")  # one launch shape for both schemes
+    own = args.workload == "batch256"  # not the batch256 block of the default run
+    if own and args.launch:  # threads,blocks_per_sm,chunk_rows
+        shape = [int(v) for v in args.launch.split(",")][:3]
+        lll.lll_batch_set_launch(b, *shape)
+        tuned = {"launch": shape, "ms": None, "tried": []}
+    elif own and args.no_tune:
+        tuned = {"launch": [0, 0, 0], "ms": None, "tried": []}
+    else:
+        tuned = autotune.tune_batch(b, inst, "full")  # one launch shape for both schemes
     lll.lll_batch_use_graph(b, True)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -777,6 +787,55 @@ def run_mappings(args, rates=None):
             "fp32_peak_basis": pk["fp32_basis"], "rows": rows}
 
 
+def run_by_length(args, rates=None):
+    """Single term structures of the 256-instance recipe, one per tenor count
+    N = 8 .. 80 (the first instance of the recipe with that N, or the nearest),
+    2^20 paths each, on the batch's launch shape (128 threads, one lane per
+    path, 16-row chunks): device time of the path kernel per scheme, the
+    throughput in path-rate-steps per second and the fraction of the FP32
+    roofline.  Short term structures do less rate work per step, so the work
+    every step and every maturity does once weighs more; the batch's cost
+    model for work items carries that as a per-step term.  Returns the JSON
+    line."""
+    import dataclasses
+
+    import torch
+
+    from paper_1006_3340_gb300 import lll
+
+    dev = torch.device("cuda", 0)
+    pk = _alu_peaks(lll, torch, dev, rates)
+    paths = args.paths or (1 << 20)
+    insts = workloads.batched_instances()
+    by_n = {}
+    for wl in insts:
+        by_n.setdefault(wl.N, wl)
+    rows = []
+    for N in (8, 12, 16, 24, 32, 40, 48, 56, 64, 72, 80):
+        wl = dataclasses.replace(by_n[min(by_n, key=lambda v: abs(v - N))], paths=paths)
+        x, W = lll.lll_build_nig_quadrature(wl.alpha, wl.beta, wl.dbar, wl.a, wl.Q)
+        sim = lll.LevyLibor(wl, x, W)
+        try:
+            sim.set_launch(128, 0, 16, 1, 1)
+            row = {"N": wl.N, "steps": wl.steps, "units_per_path": wl.units_per_path()}
+            for scheme in ("picard", "full"):
+                sim.simulate(scheme)  # warm-up
+                ms = []
+                for _ in range(max(3, args.steps)):
+                    sim.simulate(scheme)
+                    ms.append(sim.kernel_ms()[0])
+                t = statistics.median(ms)
+                ach = paths * wl.units_per_path() * 3 * wl.Q / (t * 1e-3) / 1e12
+                row[scheme] = {"kernel_ms": t, "units_per_s": paths * wl.units_per_path() / (t * 1e-3),
+                               "fp32_frac": ach / pk["fp32"]}
+            rows.append(row)
+        finally:
+            sim.close()
+    return {"metric": "path-kernel device time per tenor count", "workload": f"batch256 recipe, {paths} paths each",
+            "launch": "128 threads, one lane per path, 16-row chunks", "fp32_peak_basis": pk["fp32_basis"],
+            "rows": rows}
+
+
 def _extra_block(line):
     """The figures of another configuration kept in the headline line."""
     keep = ("value", "unit", "ms_per_step", "steps", "warmup", "config", "per_scheme", "caplets_per_s",
@@ -803,11 +862,12 @@ def main():
     ap.add_argument("--launch", default="", help="fixed launch shape for the quadrature schemes: "
                     "threads,blocks_per_sm,chunk_rows,paths_per_thread,lanes_per_path[,tenor_lanes] (no tuning)")
     ap.add_argument("--workload", default="large_single",
-                    choices=["large_single", "long_dated", "batch256", "mappings"],
+                    choices=["large_single", "long_dated", "batch256", "mappings", "by_length"],
                     help="large_single: the N=40 term structure, 2^20 paths (default); long_dated: N=120, "
                     "Q=96, 2^22 paths; batch256: 256 uneven term structures in one launch per scheme "
                     "(Picard and full only); mappings: path against tenor-parallel mapping, N=40, "
-                    "2^20 and 2^12 paths (a table, not a benchmark line)")
+                    "2^20 and 2^12 paths (a table, not a benchmark line); by_length: single term "
+                    "structures of the batch256 recipe, N = 8..80, 2^20 paths each (a table)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -833,6 +893,9 @@ def main():
     rates = lll.lll_measure_pipe_rates()
     if args.workload == "mappings":
         print(json.dumps(run_mappings(args, rates)), flush=True)
+        return 0
+    if args.workload == "by_length":
+        print(json.dumps(run_by_length(args, rates)), flush=True)
         return 0
     if args.workload == "batch256":
         line = run_batch(args, args.steps, args.warmup, not args.no_cpu_baseline, not args.no_e2e, rates)

@@ -3,13 +3,15 @@
 //
 // Each instance is an ordinary model context (lll_init builds its FP64 tables
 // on the GPU).  A simulation of the batch is one launch of batch_kernel: the
-// tiles of all instances, in instance order, are cut into one contiguous range
-// per resident block of nearly equal cost (cost of a tile = its paths times
-// s n (n+1) / 2 units), so uneven instances (N from 8 to 80, path budgets from
-// 2^12 to 2^18) keep every SM busy to the end.  A block writes one partial per
-// instance it touched; a second kernel adds the partials of each instance in
-// block order, so results are deterministic.  The launch sequence can be
-// captured once in a CUDA graph and replayed.
+// tiles of every instance are cut into work items (runs of consecutive tiles
+// of one instance) of at most 1/16 of a resident block's share of the cost,
+// and the blocks claim the items in order of decreasing cost from a counter,
+// so uneven instances (N from 8 to 80, path budgets from 2^12 to 2^18) keep
+// every SM busy to the end whatever the cost model misses.  Every item writes
+// its own partial sums; a second kernel adds the partials of each instance in
+// tile order, so results are deterministic.  The launch sequence (descriptor
+// upload, counter reset, the two kernels) can be captured once in a CUDA
+// graph and replayed.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -38,14 +40,14 @@ struct lll_batch {
     // device schedule
     PathArgs *d_desc = nullptr;
     PathArgs *h_desc = nullptr; // pinned: descriptors of the next launch
-    int *d_tile_inst = nullptr, *d_range = nullptr, *d_seg_first = nullptr;
-    uint32_t *d_tile_idx = nullptr;
+    int *d_item_inst = nullptr, *d_next = nullptr;
+    uint2 *d_item_tiles = nullptr;
     size_t *d_seg_off = nullptr;
     int *d_inst_seg_ptr = nullptr, *d_inst_segs = nullptr, *d_out_count = nullptr;
     size_t *d_out_off = nullptr;
     double *d_partials = nullptr, *d_sums = nullptr;
     float *d_state = nullptr;
-    int grid = 0, scheme = -1;
+    int grid = 0, n_items = 0, scheme = -1;
     size_t smem = 0, n_out_total = 0;
     std::vector<size_t> out_off;
     bool simulated = false, use_graph = false;
@@ -66,10 +68,10 @@ int berr(lll_batch *b, int code, const std::string &m)
 
 void free_schedule(lll_batch *b)
 {
-    cudaFree(b->d_desc); cudaFree(b->d_tile_inst); cudaFree(b->d_range); cudaFree(b->d_seg_first);
-    cudaFree(b->d_tile_idx); cudaFree(b->d_seg_off); cudaFree(b->d_inst_seg_ptr); cudaFree(b->d_inst_segs);
+    cudaFree(b->d_desc); cudaFree(b->d_item_inst); cudaFree(b->d_next); cudaFree(b->d_item_tiles);
+    cudaFree(b->d_seg_off); cudaFree(b->d_inst_seg_ptr); cudaFree(b->d_inst_segs);
     cudaFree(b->d_out_count); cudaFree(b->d_out_off); cudaFree(b->d_partials); cudaFree(b->d_state);
-    b->d_desc = nullptr; b->d_tile_inst = b->d_range = b->d_seg_first = nullptr; b->d_tile_idx = nullptr;
+    b->d_desc = nullptr; b->d_item_inst = b->d_next = nullptr; b->d_item_tiles = nullptr;
     b->d_seg_off = nullptr; b->d_inst_seg_ptr = b->d_inst_segs = b->d_out_count = nullptr;
     b->d_out_off = nullptr; b->d_partials = nullptr; b->d_state = nullptr;
     if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -103,60 +105,65 @@ int build_schedule(lll_batch *b, int scheme)
     if (e != cudaSuccess) return berr(b, LLL_ECUDA, std::string("batch kernel attributes: ") + cudaGetErrorString(e));
     if (occ < 1) return berr(b, LLL_EUNSUPPORTED, "batch kernel does not fit on an SM");
     const int bps = b->blocks_per_sm > 0 ? std::min(b->blocks_per_sm, occ) : occ;
-    // tiles in instance order with their costs
+    // Work items: runs of consecutive tiles of one instance, each of at most
+    // 1/16 of a block's share of the total cost (one tile at least).  A tile
+    // costs the same whether or not it is full (its idle lanes run along): its
+    // s n (n+1)/2 path-rate-steps, plus kStepCost of them for each of its
+    // s n steps, for what a step does once whatever the number of live rates
+    // (the increment, chunk staging and synchronisation, the maturity payoffs).
+    constexpr double kStepCost = 3.0;
     const int ni = (int)b->inst.size();
-    std::vector<int> tile_inst;
-    std::vector<uint32_t> tile_idx;
-    std::vector<double> cost;
+    std::vector<double> tile_cost(ni);
+    std::vector<uint64_t> ntile(ni);
+    double total = 0.0;
+    uint64_t ntiles = 0;
     for (int q = 0; q < ni; ++q) {
         const lll_ctx *c = b->inst[q];
-        const uint64_t nt = (b->paths[q] + T - 1) / T;
-        const double cu = (double)c->s * c->n * (c->n + 1) / 2.0;
-        for (uint64_t t = 0; t < nt; ++t) {
-            tile_inst.push_back(q);
-            tile_idx.push_back((uint32_t)t);
-            const uint64_t live = std::min<uint64_t>((uint64_t)T, b->paths[q] - t * T);
-            cost.push_back(cu * (double)live + 1.0);
+        ntile[q] = (b->paths[q] + T - 1) / T;
+        if (ntile[q] > 0xffffffffull) return berr(b, LLL_EINVAL, "instance has more than 2^32 tiles");
+        tile_cost[q] = (double)c->s * c->n * ((c->n + 1) / 2.0 + kStepCost);
+        total += tile_cost[q] * (double)ntile[q];
+        ntiles += ntile[q];
+    }
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(ntiles, (uint64_t)bps * b->sm_count));
+    const double target = total / ((double)grid * 16.0);
+    struct Item {
+        int q;
+        uint32_t t0, t1;
+        double cost;
+    };
+    std::vector<Item> items;
+    for (int q = 0; q < ni; ++q) {
+        const uint64_t per = std::max<uint64_t>(1, (uint64_t)(target / tile_cost[q]));
+        const uint64_t nit = (ntile[q] + per - 1) / per; // items of this instance, balanced sizes
+        for (uint64_t k = 0; k < nit; ++k) {
+            const uint64_t t0 = ntile[q] * k / nit, t1 = ntile[q] * (k + 1) / nit;
+            items.push_back({q, (uint32_t)t0, (uint32_t)t1, tile_cost[q] * (double)(t1 - t0)});
         }
     }
-    const int ntiles = (int)tile_inst.size();
-    const int grid = std::max(1, std::min(ntiles, bps * b->sm_count));
-    double total = 0.0;
-    for (double c : cost) total += c;
-    std::vector<int> range(grid + 1, ntiles);
-    range[0] = 0;
-    {
-        double acc = 0.0;
-        int g = 1;
-        for (int t = 0; t < ntiles && g < grid; ++t) {
-            acc += cost[t];
-            while (g < grid && acc >= total * g / grid) range[g++] = t + 1;
-        }
-        for (int gg = 1; gg <= grid; ++gg) range[gg] = std::max(range[gg], range[gg - 1]);
-        range[grid] = ntiles;
-    }
-    // segments: one per (block, instance touched), in block order
-    std::vector<int> seg_first(grid, 0), seg_inst;
-    for (int g = 0; g < grid; ++g) {
-        seg_first[g] = (int)seg_inst.size();
-        int cur = -1;
-        for (int t = range[g]; t < range[g + 1]; ++t)
-            if (tile_inst[t] != cur) { cur = tile_inst[t]; seg_inst.push_back(cur); }
-    }
-    std::vector<size_t> seg_off(seg_inst.size());
+    if (items.size() > 0x7fffffffull) return berr(b, LLL_EINVAL, "too many work items");
+    // claiming order: decreasing cost (ties in instance and tile order)
+    std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) { return x.cost > y.cost; });
+    const int nitems = (int)items.size();
+    std::vector<int> item_inst(nitems);
+    std::vector<uint2> item_tiles(nitems);
+    std::vector<size_t> seg_off(nitems);
     size_t off = 0;
-    for (size_t sg = 0; sg < seg_inst.size(); ++sg) {
-        seg_off[sg] = off;
-        const lll_ctx *c = b->inst[seg_inst[sg]];
+    for (int k = 0; k < nitems; ++k) {
+        item_inst[k] = items[k].q;
+        item_tiles[k] = make_uint2(items[k].t0, items[k].t1);
+        seg_off[k] = off;
+        const lll_ctx *c = b->inst[items[k].q];
         off += (size_t)c->n * c->ns * 2;
     }
-    // per instance: its segments in block order, and its output offset
+    // per instance: its items in tile order, and its output offset
     std::vector<int> inst_seg_ptr(ni + 1, 0), inst_segs, out_count(ni);
     std::vector<std::vector<int>> lists(ni);
-    for (size_t sg = 0; sg < seg_inst.size(); ++sg) lists[seg_inst[sg]].push_back((int)sg);
+    for (int k = 0; k < nitems; ++k) lists[items[k].q].push_back(k);
     b->out_off.assign(ni, 0);
     size_t oo = 0;
     for (int q = 0; q < ni; ++q) {
+        std::sort(lists[q].begin(), lists[q].end(), [&](int x, int y) { return items[x].t0 < items[y].t0; });
         inst_seg_ptr[q] = (int)inst_segs.size();
         inst_segs.insert(inst_segs.end(), lists[q].begin(), lists[q].end());
         b->out_off[q] = oo;
@@ -166,11 +173,11 @@ int build_schedule(lll_batch *b, int scheme)
     inst_seg_ptr[ni] = (int)inst_segs.size();
     b->n_out_total = oo;
     cudaStream_t st = b->stream;
-    bool ok = upload(&b->d_tile_inst, tile_inst, st) == cudaSuccess && upload(&b->d_tile_idx, tile_idx, st) == cudaSuccess &&
-              upload(&b->d_range, range, st) == cudaSuccess && upload(&b->d_seg_first, seg_first, st) == cudaSuccess &&
+    bool ok = upload(&b->d_item_inst, item_inst, st) == cudaSuccess && upload(&b->d_item_tiles, item_tiles, st) == cudaSuccess &&
               upload(&b->d_seg_off, seg_off, st) == cudaSuccess && upload(&b->d_inst_seg_ptr, inst_seg_ptr, st) == cudaSuccess &&
               upload(&b->d_inst_segs, inst_segs, st) == cudaSuccess && upload(&b->d_out_count, out_count, st) == cudaSuccess &&
               upload(&b->d_out_off, b->out_off, st) == cudaSuccess;
+    ok = ok && cudaMalloc((void **)&b->d_next, sizeof(int)) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&b->d_partials, sizeof(double) * std::max<size_t>(off, 1)) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&b->d_state, sizeof(float) * (size_t)grid * nst * b->n_max * T) == cudaSuccess;
     ok = ok && cudaMalloc((void **)&b->d_desc, sizeof(PathArgs) * ni) == cudaSuccess;
@@ -182,6 +189,7 @@ int build_schedule(lll_batch *b, int scheme)
     }
     for (int q = 0; q < ni; ++q) b->inst[q]->chunk_rows = CH;
     b->grid = grid;
+    b->n_items = nitems;
     b->smem = smem;
     b->scheme = scheme;
     return LLL_OK;
@@ -190,12 +198,14 @@ int build_schedule(lll_batch *b, int scheme)
 int launch_all(lll_batch *b)
 {
     BatchArgs a{};
-    a.desc = b->d_desc; a.tile_inst = b->d_tile_inst; a.tile_idx = b->d_tile_idx; a.range = b->d_range;
-    a.seg_first = b->d_seg_first; a.seg_off = b->d_seg_off; a.partials = b->d_partials; a.state = b->d_state;
-    a.n_max = b->n_max; a.ns_max = b->ns_max;
+    a.desc = b->d_desc; a.item_inst = b->d_item_inst; a.item_tiles = b->d_item_tiles; a.seg_off = b->d_seg_off;
+    a.partials = b->d_partials; a.state = b->d_state; a.next = b->d_next;
+    a.n_items = b->n_items; a.n_max = b->n_max; a.ns_max = b->ns_max;
     a.chunk_rows = b->inst[0]->chunk_rows;
     cudaStream_t st = b->stream;
     cudaError_t e = cudaMemcpyAsync(b->d_desc, b->h_desc, sizeof(PathArgs) * b->inst.size(), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaMemsetAsync(b->d_next, 0, sizeof(int), st);
     if (e != cudaSuccess) return (int)e;
     e = (cudaError_t)launch_batch_kernel(b->scheme, b->QP, b->grid, b->threads, b->smem, st, a);
     if (e != cudaSuccess) return (int)e;

@@ -143,16 +143,132 @@ __device__ __forceinline__ void maturity_products_grouped(const PathArgs &a, int
     Lm = expf(z(m));
 }
 
+// Caplet payoff, Eq. (caplet), discounted under the terminal measure:
+// delta B(0,T_N) prod_{l>m} (1 + delta L_l) (L_m - K)^+, with P the product.
+// An FP32 number.
+__device__ __forceinline__ float caplet_payoff(const PathArgs &a, float P, float Lm, float K)
+{
+    return a.dBN * P * fmaxf(Lm - K, 0.0f);
+}
+
 // Discounted payoff (under the terminal measure, times B(0, T_N)) at T_m for
-// strike K.  Caplet, Eq. (caplet): delta B(0,T_N) prod_{l>m} (1 + delta L_l) (L_m - K)^+.
+// strike K.  Caplet: caplet_payoff.
 // Co-terminal payer swaption on the swap over [T_m, T_N]: its value at T_m is
 // (1 - B(T_m,T_N) - K delta sum_{j>m} B(T_m,T_j))^+, and divided by the
 // numeraire B(T_m, T_N) it is ((1 + delta L_m) P - 1 - K delta S)^+.
 __device__ __forceinline__ double payoff(const PathArgs &a, double P, double S, float Lm, float K)
 {
-    if (a.product == 0) return (double)(a.dBN * (float)P * fmaxf(Lm - K, 0.0f));
+    if (a.product == 0) return (double)caplet_payoff(a, (float)P, Lm, K);
     const double X = (1.0 + (double)(a.delta * Lm)) * P - 1.0 - (double)K * (double)a.delta * S;
     return X > 0.0 ? (double)a.dBN / (double)a.delta * X : 0.0;
+}
+
+// ---- A warp's payoff sums without FP64 arithmetic --------------------------
+// GB300 issues FP64 arithmetic at about 1/64 of the FP32 rate (1.25 against
+// 80 TFLOP/s nominal), and a warp's sums of its paths' payoffs and squared
+// payoffs, formed at every maturity for every strike, are the path kernels'
+// only FP64 work per path (ncu: the FP64 pipe 8 % busy in the Picard path
+// kernel on the N = 40 workload when they were FP64 sums).  Caplet payoffs are FP32
+// numbers, so their sums are kept as unevaluated pairs hi + lo of FP32
+// numbers ("double-float"):
+//  * TwoSum (Knuth, TAOCP vol. 2, 4.2.2) gives the exact rounding error of an
+//    FP32 addition;
+//  * the FMA form of Dekker's product (Dekker 1971) gives v * v exactly as
+//    fl(v v) + fma(v, v, -fl(v v));
+//  * after each addition the pair is renormalised by Dekker's Fast2Sum.
+// Adding two pairs this way has a relative error below 3 * 2^-48 when both
+// have one sign (Joldes, Muller and Popescu 2017, "Tight and rigorous error
+// bounds for basic building blocks of double-word arithmetic"); payoffs are
+// non-negative, so the five levels of the butterfly keep a warp's sums within
+// about 6e-14 of the exact ones.  The block reduction adds the warps' pairs
+// the same way and turns the result into FP64 (hi + lo) once per strike and
+// maturity.
+struct DFloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DFloat df_add(DFloat a, DFloat b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float e = ((a.hi - (s - bb)) + (b.hi - bb)) + (a.lo + b.lo);
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ DFloat df_square(float v)
+{
+    const float p = v * v;
+    return {p, fmaf(v, v, -p)};
+}
+
+__device__ __forceinline__ DFloat df_warp_sum(DFloat v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = df_add(v, DFloat{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+    return v;
+}
+
+// Sums over the warp of the caplet payoffs v of every lane's paths (0 for a
+// path that is not simulated) and of v^2: (sum hi, sum lo, sum2 hi, sum2 lo),
+// the same on every lane.
+__device__ __forceinline__ float4 caplet_warp_sums_inline(DFloat s1, DFloat s2)
+{
+    s1 = df_warp_sum(s1);
+    s2 = df_warp_sum(s2);
+    return make_float4(s1.hi, s1.lo, s2.hi, s2.lo);
+}
+
+// The same as calls.  They stay out of line on purpose: inlined into the
+// path kernel, this code (like a plain FP32 shuffle sum in its place) changed
+// the code generated for the kernel's rate sweep, which then ran 7 % slower
+// (Picard, N = 40 workload, 2^20 paths: 64.3 ms inlined, 59.7 ms as a call,
+// 60.3 ms with the former FP64 sums).
+static __device__ __noinline__ float4 caplet_warp_sums1(float v)
+{
+    return caplet_warp_sums_inline(DFloat{v, 0.0f}, df_square(v));
+}
+
+static __device__ __noinline__ float4 caplet_warp_sums2(float v0, float v1)
+{
+    return caplet_warp_sums_inline(df_add(DFloat{v0, 0.0f}, DFloat{v1, 0.0f}), df_add(df_square(v0), df_square(v1)));
+}
+
+template <int R>
+__device__ __forceinline__ float4 caplet_warp_sums(const float (&v)[R])
+{
+    static_assert(R == 1 || R == 2, "one or two paths per lane");
+    if constexpr (R == 1) return caplet_warp_sums1(v[0]);
+    else return caplet_warp_sums2(v[0], v[1]);
+}
+
+// The sums over warps 0 .. nw-1 of a block for strike q, from the block's
+// reduction buffer of 16-byte slots [warp][ns] (caplets: the four floats of
+// caplet_warp_sums, added as pairs in warp order and turned into FP64 once;
+// swaptions: the FP64 sums of v and v^2, added in warp order).
+__device__ __forceinline__ void block_payoff_sums(const PathArgs &a, const double *red, int nw, int ns, int q,
+                                                  double &s1, double &s2)
+{
+    if (a.product == 0) {
+        const float4 *r4 = reinterpret_cast<const float4 *>(red);
+        float4 r = r4[q];
+        DFloat x{r.x, r.y}, y{r.z, r.w};
+        for (int wv = 1; wv < nw; ++wv) {
+            r = r4[(size_t)wv * ns + q];
+            x = df_add(x, DFloat{r.x, r.y});
+            y = df_add(y, DFloat{r.z, r.w});
+        }
+        s1 = (double)x.hi + (double)x.lo;
+        s2 = (double)y.hi + (double)y.lo;
+    } else {
+        s1 = 0.0;
+        s2 = 0.0;
+        for (int wv = 0; wv < nw; ++wv) {
+            s1 += red[2 * ((size_t)wv * ns + q) + 0];
+            s2 += red[2 * ((size_t)wv * ns + q) + 1];
+        }
+    }
 }
 
 }  // namespace lll

@@ -42,14 +42,13 @@ struct PathArgs {
 // Many instances in one persistent launch (see batch_kernel in lll_paths.cu).
 struct BatchArgs {
     const PathArgs *desc;    // [n_inst] per-instance arguments (state/partials unused)
-    const int *tile_inst;    // [tiles] instance of each tile, instance-ordered
-    const uint32_t *tile_idx;// [tiles] tile index within its instance
-    const int *range;        // [grid+1] tile range of each block
-    const int *seg_first;    // [grid] first output segment of each block
-    const size_t *seg_off;   // [segments] offset (doubles) of each segment in partials
-    double *partials;        // segment outputs: [n][ns][2] per segment
+    const int *item_inst;    // [items] instance of each work item (items in claiming order)
+    const uint2 *item_tiles; // [items] tile range [x, y) of the item within its instance
+    const size_t *seg_off;   // [items] offset (doubles) of each item's output in partials
+    double *partials;        // item outputs: [n][ns][2] per item
     float *state;            // [grid][NST][n_max][threads]
-    int n_max, ns_max, chunk_rows;
+    int *next;               // claim counter, 0 at launch
+    int n_items, n_max, ns_max, chunk_rows;
 };
 
 // The launch lll_simulate would make for one simulation, worked out without

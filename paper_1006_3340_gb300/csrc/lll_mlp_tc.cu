@@ -441,6 +441,16 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                                           Pp[gi], Sp[gi], Lm[gi]);
                     for (int qs = 0; qs < ns; ++qs) {
                         const float K = a.strikes[(size_t)(m - 1) * ns + qs];
+                        const size_t slot = ((size_t)buf * 4 + q4) * ns + qs;
+                        if (a.product == 0) {
+                            float v[kGroups];
+#pragma unroll
+                            for (int gi = 0; gi < kGroups; ++gi)
+                                v[gi] = active[gi] ? caplet_payoff(a, (float)Pp[gi], Lm[gi], K) : 0.0f;
+                            const float4 r = caplet_warp_sums(v);
+                            if (lane == 0) reinterpret_cast<float4 *>(red)[slot] = r;
+                            continue;
+                        }
                         double s1 = 0.0, s2 = 0.0;
 #pragma unroll
                         for (int gi = 0; gi < kGroups; ++gi) {
@@ -451,24 +461,19 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_kernel(const PathArgs a, c
                         s1 = warp_sum(s1);
                         s2 = warp_sum(s2);
                         if (lane == 0) {
-                            red[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 0] = s1;
-                            red[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 1] = s2;
+                            red[2 * slot + 0] = s1;
+                            red[2 * slot + 1] = s2;
                         }
                     }
                     if (lane == 0) mbar_arrive(&payb[0]);
                     if (q4 == 0) {
                         if (!warp_wait(&payb[0], php, abort, g.err)) { ok = false; break; }
-                        if (lane == 0) {
-                            for (int qs = 0; qs < ns; ++qs) {
-                                double s1 = 0.0, s2 = 0.0;
-                                for (int wv = 0; wv < 4; ++wv) {
-                                    s1 += red[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 0];
-                                    s2 += red[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 1];
-                                }
-                                double *acc = bsum + 4 * ((size_t)(m - 1) * ns + qs);
-                                kahan_add(acc + 0, acc + 1, s1);
-                                kahan_add(acc + 2, acc + 3, s2);
-                            }
+                        for (int qs = lane; qs < ns; qs += 32) { // one strike per lane
+                            double s1, s2;
+                            block_payoff_sums(a, red + (size_t)buf * 4 * ns * 2, 4, ns, qs, s1, s2);
+                            double *acc = bsum + 4 * ((size_t)(m - 1) * ns + qs);
+                            kahan_add(acc + 0, acc + 1, s1);
+                            kahan_add(acc + 2, acc + 3, s2);
                         }
                     }
                     php ^= 1;
@@ -830,6 +835,16 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
                                                   Pp[gi], Sp[gi], Lm[gi]);
                     for (int qs = 0; qs < ns; ++qs) {
                         const float K = a.strikes[(size_t)(m - 1) * ns + qs];
+                        const size_t slot = ((size_t)buf * 4 + q4) * ns + qs;
+                        if (a.product == 0) {
+                            float v[kGroups];
+#pragma unroll
+                            for (int gi = 0; gi < kGroups; ++gi)
+                                v[gi] = lp0 + gi * kRows < a.paths ? caplet_payoff(a, (float)Pp[gi], Lm[gi], K) : 0.0f;
+                            const float4 r = caplet_warp_sums(v);
+                            if (lane == 0) reinterpret_cast<float4 *>(red)[slot] = r;
+                            continue;
+                        }
                         double s1 = 0.0, s2 = 0.0;
 #pragma unroll
                         for (int gi = 0; gi < kGroups; ++gi) {
@@ -840,24 +855,19 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_tc_vec_kernel(const PathArgs 
                         s1 = warp_sum(s1);
                         s2 = warp_sum(s2);
                         if (lane == 0) {
-                            red[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 0] = s1;
-                            red[(((size_t)buf * 4 + q4) * ns + qs) * 2 + 1] = s2;
+                            red[2 * slot + 0] = s1;
+                            red[2 * slot + 1] = s2;
                         }
                     }
                     if (lane == 0) mbar_arrive(payb);
                     if (q4 == 0) {
                         if (!warp_wait(payb, php, abort, g.err)) { ok = false; break; }
-                        if (lane == 0) {
-                            for (int qs = 0; qs < ns; ++qs) {
-                                double s1 = 0.0, s2 = 0.0;
-                                for (int wv = 0; wv < 4; ++wv) {
-                                    s1 += red[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 0];
-                                    s2 += red[(((size_t)buf * 4 + wv) * ns + qs) * 2 + 1];
-                                }
-                                double *acc = bsum + 4 * ((size_t)(m - 1) * ns + qs);
-                                kahan_add(acc + 0, acc + 1, s1);
-                                kahan_add(acc + 2, acc + 3, s2);
-                            }
+                        for (int qs = lane; qs < ns; qs += 32) { // one strike per lane
+                            double s1, s2;
+                            block_payoff_sums(a, red + (size_t)buf * 4 * ns * 2, 4, ns, qs, s1, s2);
+                            double *acc = bsum + 4 * ((size_t)(m - 1) * ns + qs);
+                            kahan_add(acc + 0, acc + 1, s1);
+                            kahan_add(acc + 2, acc + 3, s2);
                         }
                     }
                     php ^= 1;

@@ -25,8 +25,8 @@
 //
 // At T_m (end of step m*s-1) the caplet payoff of Eq. (caplet),
 //     delta B(0,T_N) prod_{l>m} (1 + delta L_l(T_m)) (L_m(T_m) - K)^+,
-// is reduced over the block (warp shuffles, then warps in fixed order) into
-// FP64 Kahan accumulators; per-block partials are summed in fixed order by a
+// is reduced over the block (warp shuffles in double-float FP32 pairs, then
+// warps in fixed order in FP64) into FP64 Kahan accumulators; per-block partials are summed in fixed order by a
 // second kernel, so results are run-to-run deterministic.
 //
 // Layout: the per-step table rows (k, i) of the live rates are staged into
@@ -84,7 +84,7 @@ struct Smem {
     float2 *cn;   // [QP/2] c_j = W_j / x_j^2
     float *c0;    // [n]
     double *bsum; // [n * ns][4]: sum, comp, sumsq, comp
-    double *red;  // [warps][ns][2]
+    double *red;  // [warps][ns] 16-byte slots (block_payoff_sums)
 };
 
 __host__ __device__ inline size_t align16(size_t v) { return (v + 15) & ~size_t(15); }
@@ -310,27 +310,33 @@ __device__ __forceinline__ void run_tile(const PathArgs &a, const Smem &sm, floa
                     }, Pp[u], Sp[u], Lm[u]);
                 for (int q = 0; q < ns; ++q) {
                     const float K = a.strikes[(size_t)(m - 1) * ns + q];
-                    double pay = 0.0, pay2 = 0.0;
+                    const size_t slot = (size_t)warp * ns + q;
+                    if (a.product == 0) {
+                        float v[R];
 #pragma unroll
-                    for (int u = 0; u < R; ++u) {
-                        const double v = active[u] ? payoff(a, Pp[u], Sp[u], Lm[u], K) : 0.0;
-                        pay += v;
-                        pay2 += v * v;
-                    }
-                    const double s1 = warp_sum(pay);
-                    const double s2 = warp_sum(pay2);
-                    if (lane == 0) {
-                        sm.red[((size_t)warp * ns + q) * 2 + 0] = s1;
-                        sm.red[((size_t)warp * ns + q) * 2 + 1] = s2;
+                        for (int u = 0; u < R; ++u) v[u] = active[u] ? caplet_payoff(a, (float)Pp[u], Lm[u], K) : 0.0f;
+                        const float4 r = caplet_warp_sums(v);
+                        if (lane == 0) reinterpret_cast<float4 *>(sm.red)[slot] = r;
+                    } else {
+                        double pay = 0.0, pay2 = 0.0;
+#pragma unroll
+                        for (int u = 0; u < R; ++u) {
+                            const double v = active[u] ? payoff(a, Pp[u], Sp[u], Lm[u], K) : 0.0;
+                            pay += v;
+                            pay2 += v * v;
+                        }
+                        const double s1 = warp_sum(pay);
+                        const double s2 = warp_sum(pay2);
+                        if (lane == 0) {
+                            sm.red[2 * slot + 0] = s1;
+                            sm.red[2 * slot + 1] = s2;
+                        }
                     }
                 }
                 __syncthreads();
                 if (tid < ns) {
-                    double s1 = 0.0, s2 = 0.0;
-                    for (int wv = 0; wv < (T >> 5); ++wv) {
-                        s1 += sm.red[((size_t)wv * ns + tid) * 2 + 0];
-                        s2 += sm.red[((size_t)wv * ns + tid) * 2 + 1];
-                    }
+                    double s1, s2;
+                    block_payoff_sums(a, sm.red, T >> 5, ns, tid, s1, s2);
                     double *acc = sm.bsum + 4 * ((size_t)(m - 1) * ns + tid);
                     kahan_add(acc + 0, acc + 1, s1);
                     kahan_add(acc + 2, acc + 3, s2);
@@ -375,11 +381,14 @@ __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks) path_
     }
 }
 
-// Many independent term structures in one persistent launch.  Block g
-// processes the tiles [range[g], range[g+1]) of a cost-balanced, instance-
-// ordered tile list; whenever it leaves an instance it writes that instance's
-// payoff partials to its own segment, so the final sums (per instance, over
-// segments in block order) are deterministic.
+// Many independent term structures in one persistent launch.  The work is a
+// list of items -- a range of consecutive tiles of one instance -- sorted by
+// decreasing cost; every block claims the next item from a counter until the
+// list is exhausted, so the longest items start first and the short ones fill
+// the end (longest-processing-time-first list scheduling, Graham 1969).  Each
+// item writes its payoff sums to its own segment, and a second kernel adds the
+// segments of each instance in tile order, so the results do not depend on
+// which block ran which item.
 template <int SCHEME, int QP>
 __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchArgs b)
 {
@@ -388,33 +397,29 @@ __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchArgs b)
     const int T = blockDim.x, tid = threadIdx.x;
     const Smem sm = carve(smem_raw, QP, b.n_max, b.ns_max, T, b.chunk_rows);
     float *st = b.state + (size_t)blockIdx.x * NST * b.n_max * T + tid;
-    int cur = -1, seg = b.seg_first[blockIdx.x];
+    int cur = -1;
     __shared__ PathArgs sa; // the current instance's arguments
+    __shared__ int claimed;
     const PathArgs *a = &sa;
-    for (int t = b.range[blockIdx.x]; t < b.range[blockIdx.x + 1]; ++t) {
-        const int q = b.tile_inst[t];
+    for (;;) {
+        __syncthreads(); // the previous item's outputs are written, `claimed` read
+        if (tid == 0) claimed = atomicAdd(b.next, 1);
+        __syncthreads();
+        const int it = claimed;
+        if (it >= b.n_items) break;
+        const int q = b.item_inst[it];
         if (q != cur) {
-            if (cur >= 0) {
-                __syncthreads();
-                double *out = b.partials + b.seg_off[seg++];
-                for (int e = tid; e < a->n * a->ns; e += T) {
-                    out[2 * e + 0] = sm.bsum[4 * e + 0];
-                    out[2 * e + 1] = sm.bsum[4 * e + 2];
-                }
-            }
             cur = q;
-            __syncthreads();
             if (tid == 0) sa = b.desc[q];
             __syncthreads();
             for (int e = tid; e < a->n; e += T) sm.c0[e] = a->c0[e];
             for (int e = tid; e < QP; e += T) reinterpret_cast<float *>(sm.cn)[e] = a->cn[e];
-            for (int e = tid; e < 4 * a->n * a->ns; e += T) sm.bsum[e] = 0.0;
         }
-        run_tile<SCHEME, QP, 1>(*a, sm, st, b.tile_idx[t]);
-    }
-    if (cur >= 0) {
+        for (int e = tid; e < 4 * a->n * a->ns; e += T) sm.bsum[e] = 0.0;
+        const uint2 tr = b.item_tiles[it];
+        for (uint32_t t = tr.x; t < tr.y; ++t) run_tile<SCHEME, QP, 1>(*a, sm, st, t);
         __syncthreads();
-        double *out = b.partials + b.seg_off[seg];
+        double *out = b.partials + b.seg_off[it];
         for (int e = tid; e < a->n * a->ns; e += T) {
             out[2 * e + 0] = sm.bsum[4 * e + 0];
             out[2 * e + 1] = sm.bsum[4 * e + 2];

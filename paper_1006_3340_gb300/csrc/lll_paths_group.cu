@@ -272,21 +272,25 @@ __global__ void __launch_bounds__(kMaxThreads, (QP <= 64 ? 2 : 1)) group_kernel(
                 }, Pp, Sp, Lm);
                 for (int q = 0; q < ns; ++q) {
                     const float K = a.strikes[(size_t)(m - 1) * ns + q];
-                    const double pay = active ? payoff(a, Pp, Sp, Lm, K) : 0.0;
-                    const double s1 = warp_sum(pay);
-                    const double s2 = warp_sum(pay * pay);
-                    if (lane == 0) {
-                        red[((size_t)warp * ns + q) * 2 + 0] = s1;
-                        red[((size_t)warp * ns + q) * 2 + 1] = s2;
+                    const size_t slot = (size_t)warp * ns + q;
+                    if (a.product == 0) {
+                        const float v[1] = {active ? caplet_payoff(a, (float)Pp, Lm, K) : 0.0f};
+                        const float4 r = caplet_warp_sums(v);
+                        if (lane == 0) reinterpret_cast<float4 *>(red)[slot] = r;
+                    } else {
+                        const double pay = active ? payoff(a, Pp, Sp, Lm, K) : 0.0;
+                        const double s1 = warp_sum(pay);
+                        const double s2 = warp_sum(pay * pay);
+                        if (lane == 0) {
+                            red[2 * slot + 0] = s1;
+                            red[2 * slot + 1] = s2;
+                        }
                     }
                 }
                 __syncthreads();
                 if (tid < ns) {
-                    double s1 = 0.0, s2 = 0.0;
-                    for (int wv = 0; wv < (T >> 5); ++wv) {
-                        s1 += red[((size_t)wv * ns + tid) * 2 + 0];
-                        s2 += red[((size_t)wv * ns + tid) * 2 + 1];
-                    }
+                    double s1, s2;
+                    block_payoff_sums(a, red, T >> 5, ns, tid, s1, s2);
                     double *acc = bsum + 4 * ((size_t)(m - 1) * ns + tid);
                     kahan_add(acc + 0, acc + 1, s1);
                     kahan_add(acc + 2, acc + 3, s2);

@@ -2,9 +2,11 @@
 
 Each instance q draws from its own Philox stream (counter word 1 = q), so it
 is checked against the FP64 oracle run with instance q: prices within 1e-7.
-The CUDA-graph replay must reproduce the eager launch exactly, and the
-cost-balanced schedule must give the same sums whatever the launch shape
-(within FP64 rounding of the different partial grouping).
+The CUDA-graph replay must reproduce the eager launch exactly (the blocks
+claim work items from a counter, in whatever order they get to it, and the
+results must not depend on it), and the schedule must give the same sums
+whatever the launch shape (within FP64 rounding of the different grouping of
+the partial sums).
 """
 import numpy as np
 import pytest
@@ -79,3 +81,40 @@ def test_graph_replay_and_launch_shapes(lll):
             assert np.allclose(pe, ps, rtol=1e-12, atol=1e-18)
     finally:
         lll.lll_batch_destroy(b)
+
+
+def test_claimed_items_run_every_tile_once(lll):
+    """About 2^21 paths over 8 instances: many more tiles than resident blocks,
+    so items span several tiles and every block claims many of them, in an
+    order that changes from launch to launch.  Repeated launches give
+    bit-identical prices; instance 0 (Philox word 1 = 0, as a single context
+    draws) equals its own single-context simulation of the same paths, and
+    every instance equals a launch with 64-thread tiles (other tiles, other
+    items), both within FP64 rounding of the grouping -- a tile run twice or
+    not at all would move a price by about 1/(tiles of the instance)."""
+    inst = _instances(8, 1 << 21, seed=13)
+    b, keep = lll.lll_batch_init(inst)
+    try:
+        runs = []
+        for _ in range(3):
+            lll.lll_batch_simulate(b, lll.LLL_FULL, 5)
+            runs.append(_prices(lll, b, inst))
+        lll.lll_batch_set_launch(b, 64, 0, 0)
+        lll.lll_batch_simulate(b, lll.LLL_FULL, 5)
+        small = _prices(lll, b, inst)
+    finally:
+        lll.lll_batch_destroy(b)
+    for r in runs[1:]:
+        for (p0, _), (p1, _) in zip(runs[0], r):
+            assert np.array_equal(p0, p1)
+    for q, ((p0, _), (ps, _)) in enumerate(zip(runs[0], small)):
+        assert np.allclose(p0, ps, rtol=1e-12, atol=1e-18), q
+    wl, x, W = inst[0]
+    sim = lll.LevyLibor(wl, x, W)
+    try:
+        sim.set_launch(128, 0, 0, 1, 1)  # one lane per path: the batch kernel's arithmetic
+        sim.simulate("full", seed=5)
+        p, _ = sim.prices()
+    finally:
+        sim.close()
+    assert np.allclose(runs[0][0][0], p, rtol=1e-12, atol=1e-18)

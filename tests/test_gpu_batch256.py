@@ -10,7 +10,7 @@ checked against the FP64 oracle run with instance q:
     the Picard scheme (the configuration's scheme), and those with N <= 40
     under the full scheme, within 1e-7;
   * four paths sampled across every instance's budget (so they fall in
-    different tiles and blocks of the cost-balanced schedule), and 32 of the
+    different tiles and work items of the schedule), and 32 of the
     N = 80 instance, within 1e-5 relative on every recorded rate.
 """
 import numpy as np
