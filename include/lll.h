@@ -237,8 +237,11 @@ int lll_build_nig_quadrature(lll_nig nig, double xmax, int Q, double *nodes, dou
 
 /* ---- Batches of independent term structures -------------------------------
  * Many models (uneven tenor counts, curves, volatilities, NIG parameters,
- * strike grids and path budgets) simulated by one persistent launch whose
- * tiles are balanced by cost across the SMs.  Instance q draws its increments
+ * strike grids and path budgets) simulated by one persistent launch: the
+ * resident blocks claim work items (runs of one instance's 128-path tiles) in
+ * order of decreasing cost until none is left, and each instance's results
+ * are summed in tile order, so they are the same from launch to launch
+ * whatever block ran which item.  Instance q draws its increments
  * from Philox counter (k, q, p_lo, p_hi): independent streams per instance.
  * All instances must use the NIG driver and the same padded Q (16, 32, 64, 96
  * or 128). */
@@ -268,8 +271,9 @@ int lll_batch_init(lll_batch **out, int n_inst, const lll_instance *inst, void *
 int lll_batch_set_launch(lll_batch *b, int threads_per_block, int blocks_per_sm, int chunk_rows);
 
 /* lll_batch_use_graph -- enable: the first simulation of a scheme captures
- * its launch sequence (descriptor upload from pinned memory, batch kernel,
- * final reduction) in a CUDA graph; later ones replay it. */
+ * its launch sequence (descriptor upload from pinned memory, reset of the
+ * work-item counter, batch kernel, final reduction) in a CUDA graph; later
+ * ones replay it. */
 int lll_batch_use_graph(lll_batch *b, int enable);
 
 /* lll_batch_simulate -- all instances, scheme LLL_FULL or LLL_PICARD, one
