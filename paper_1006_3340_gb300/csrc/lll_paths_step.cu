@@ -57,17 +57,38 @@ __global__ void __launch_bounds__(kSpT) sp_draw(const PathArgs a, uint64_t chunk
     dH[e] = draw_increment(a, a.first_path + chunk_first + lp, (uint32_t)k);
 }
 
-// thread (l, path): Y[k][l][p] = sum_{m<k} lambda_l(m) dH_m for k < l s
-__global__ void __launch_bounds__(kSpT) sp_scan_y(const PathArgs a, int Pc, const float *dH, float *Y)
+// thread (l, path): Y[k][l][p] = sum_{m<k} lambda_l(m) dH_m for k < l s.
+// The running sum is a dependent chain, so the loads of eight steps are issued
+// ahead of their additions (same operations in the same order): one load
+// latency per eight steps instead of one per step.
+__global__ void __launch_bounds__(kSpT) sp_scan_y(const PathArgs a, int Pc, const float *__restrict__ dH,
+                                                  float *__restrict__ Y)
 {
+    constexpr int U = 8;
     const size_t e = (size_t)blockIdx.x * kSpT + threadIdx.x;
     const int n = a.n;
     if (e >= (size_t)n * Pc) return;
     const int l = (int)(e / Pc) + 1, lp = (int)(e % Pc);
+    const int K = l * a.s;
+    const float *lam = reinterpret_cast<const float *>(a.row + (l - 1)); // .x of row (k, l): + 4 k n
     float y = 0.0f;
-    for (int k = 0; k < l * a.s; ++k) {
+    int k = 0;
+    for (; k + U <= K; k += U) {
+        float lv[U], dv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            lv[u] = __ldg(lam + (size_t)4 * (k + u) * n);
+            dv[u] = __ldg(dH + (size_t)(k + u) * Pc + lp);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            Y[((size_t)(k + u) * n + (l - 1)) * Pc + lp] = y;
+            y = fmaf(lv[u], dv[u], y);
+        }
+    }
+    for (; k < K; ++k) {
         Y[((size_t)k * n + (l - 1)) * Pc + lp] = y;
-        y = fmaf(a.row[(size_t)k * n + (l - 1)].x, dH[(size_t)k * Pc + lp], y);
+        y = fmaf(__ldg(lam + (size_t)4 * k * n), __ldg(dH + (size_t)k * Pc + lp), y);
     }
 }
 
@@ -125,10 +146,14 @@ __global__ void __launch_bounds__(kSpT) sp_sweep(const PathArgs a, int Pc, const
 }
 
 // thread (i, path): running sums of the drift and of lambda dH; at every
-// maturity T_m (m <= i) the log-rate log L_i(T_m) into Zm[m-1][i-1][p].
-__global__ void __launch_bounds__(kSpT) sp_scan_d(const PathArgs a, int Pc, uint64_t chunk_first, const float *dH,
-                                                  const float *Y, const float *Bh, float *Zm)
+// maturity T_m (m <= i) the log-rate log L_i(T_m) into Zm[m-1][i-1][p].  The
+// drift terms of sixteen steps are loaded ahead of their additions (same
+// operations in the same order), as in sp_scan_y.
+__global__ void __launch_bounds__(kSpT) sp_scan_d(const PathArgs a, int Pc, uint64_t chunk_first,
+                                                  const float *__restrict__ dH, const float *__restrict__ Y,
+                                                  const float *__restrict__ Bh, float *__restrict__ Zm)
 {
+    constexpr int U = 16;
     const size_t e = (size_t)blockIdx.x * kSpT + threadIdx.x;
     const int n = a.n, s = a.s;
     if (e >= (size_t)n * Pc) return;
@@ -136,19 +161,30 @@ __global__ void __launch_bounds__(kSpT) sp_scan_d(const PathArgs a, int Pc, uint
     const uint64_t gp = chunk_first + lp; // path index within the simulation
     uint64_t sidx = ~0ull;
     if (a.snap != nullptr && gp % a.snap_stride == 0 && gp / a.snap_stride < a.n_snap) sidx = gp / a.snap_stride;
+    const int K = i * s;
     float d = 0.0f;
-    for (int k = 0; k < i * s; ++k) {
-        const size_t ki = ((size_t)k * n + (i - 1)) * Pc + lp;
-        d = d + Bh[ki];
-        if ((k + 1) % s == 0) {
-            const int m = (k + 1) / s;
-            // int lambda_i dH up to T_m: the stored prefix at step m s, or for the
-            // last step of rate i the same update as the one-lane kernel's
-            const float y = m < i ? Y[((size_t)(k + 1) * n + (i - 1)) * Pc + lp]
-                                  : fmaf(a.row[(size_t)k * n + (i - 1)].x, dH[(size_t)k * Pc + lp], Y[ki]);
-            const float z = y + d + a.Z0[i - 1];
-            Zm[((size_t)(m - 1) * n + (i - 1)) * Pc + lp] = z;
-            if (sidx != ~0ull) a.snap[((size_t)(m - 1) * n + (i - 1)) * a.snap_pitch + sidx] = z;
+    for (int k0 = 0; k0 < K; k0 += U) {
+        float b[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            b[u] = k0 + u < K ? __ldg(Bh + ((size_t)(k0 + u) * n + (i - 1)) * Pc + lp) : 0.0f;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u;
+            if (k >= K) break;
+            d = d + b[u];
+            if ((k + 1) % s == 0) {
+                const int m = (k + 1) / s;
+                // int lambda_i dH up to T_m: the stored prefix at step m s, or for the
+                // last step of rate i the same update as the one-lane kernel's
+                const size_t ki = ((size_t)k * n + (i - 1)) * Pc + lp;
+                const float y = m < i ? __ldg(Y + ((size_t)(k + 1) * n + (i - 1)) * Pc + lp)
+                                      : fmaf(a.row[(size_t)k * n + (i - 1)].x, __ldg(dH + (size_t)k * Pc + lp),
+                                             __ldg(Y + ki));
+                const float z = y + d + a.Z0[i - 1];
+                Zm[((size_t)(m - 1) * n + (i - 1)) * Pc + lp] = z;
+                if (sidx != ~0ull) a.snap[((size_t)(m - 1) * n + (i - 1)) * a.snap_pitch + sidx] = z;
+            }
         }
     }
 }
@@ -158,7 +194,7 @@ __global__ void __launch_bounds__(kSpT) sp_scan_d(const PathArgs a, int Pc, uint
 __global__ void __launch_bounds__(kSpT) sp_payoff(const PathArgs a, int Pc, uint64_t chunk_first, const float *Zm,
                                                   int block0, double *partials)
 {
-    __shared__ double red[kSpT / 32][64][2];
+    __shared__ __align__(16) double red[kSpT / 32 * 64 * 2]; // [warp][strike] 16-byte slots
     const int n = a.n, ns = a.ns, m = blockIdx.y + 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int lp = blockIdx.x * kSpT + threadIdx.x;
@@ -169,20 +205,24 @@ __global__ void __launch_bounds__(kSpT) sp_payoff(const PathArgs a, int Pc, uint
         maturity_products(a, m, [&](int i) { return Zm[((size_t)(m - 1) * n + (i - 1)) * Pc + lp]; }, Pp, Sp, Lm);
     for (int q = 0; q < ns; ++q) {
         const float K = a.strikes[(size_t)(m - 1) * ns + q];
-        const double v = active ? payoff(a, Pp, Sp, Lm, K) : 0.0;
-        const double s1 = warp_sum(v), s2 = warp_sum(v * v);
-        if (lane == 0) {
-            red[warp][q][0] = s1;
-            red[warp][q][1] = s2;
+        const size_t slot = (size_t)warp * ns + q;
+        if (a.product == 0) {
+            const float v[1] = {active ? caplet_payoff(a, (float)Pp, Lm, K) : 0.0f};
+            const float4 r = caplet_warp_sums(v);
+            if (lane == 0) reinterpret_cast<float4 *>(red)[slot] = r;
+        } else {
+            const double v = active ? payoff(a, Pp, Sp, Lm, K) : 0.0;
+            const double s1 = warp_sum(v), s2 = warp_sum(v * v);
+            if (lane == 0) {
+                red[2 * slot + 0] = s1;
+                red[2 * slot + 1] = s2;
+            }
         }
     }
     __syncthreads();
     if (threadIdx.x < ns) {
-        double s1 = 0.0, s2 = 0.0;
-        for (int w = 0; w < kSpT / 32; ++w) {
-            s1 += red[w][threadIdx.x][0];
-            s2 += red[w][threadIdx.x][1];
-        }
+        double s1, s2;
+        block_payoff_sums(a, red, kSpT / 32, ns, threadIdx.x, s1, s2);
         double *out = partials + ((size_t)(block0 + blockIdx.x) * n + (m - 1)) * ns * 2 + 2 * threadIdx.x;
         out[0] = s1;
         out[1] = s2;

@@ -74,13 +74,6 @@ __device__ __forceinline__ void kahan_add(double *s, double *c, double x)
     *s = t;
 }
 
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
 __host__ __device__ inline size_t a16(size_t v) { return (v + 15) & ~size_t(15); }
 
 // Shared-memory plan (bytes); PB = paths per block, pitch PB + 1 floats.
@@ -93,7 +86,7 @@ struct TenorSmem {
     float *sb;    // [n][PB + 1]: PICARD drift integral
     float *sw;    // [n][PB + 1]: weights of the step
     double *bsum; // [n * ns][4]
-    double *red;  // [warps][ns][2]
+    double *red;  // [warps][ns] 16-byte slots (caplet_warp_sums)
 };
 
 __host__ __device__ inline size_t tenor_smem_bytes(int QP, int n, int ns, int T, int G)
@@ -296,21 +289,16 @@ __global__ void __launch_bounds__(kTenorThreads) tenor_kernel(const PathArgs a, 
                         a.snap[((size_t)(m - 1) * n + (i - 1)) * a.snap_pitch + sidx] = zoff(i) + a.Z0[i - 1];
                 for (int q = 0; q < ns; ++q) {
                     const float K = a.strikes[(size_t)(m - 1) * ns + q];
-                    const double v = (owner && active) ? (double)(a.dBN * Pf * fmaxf(Lm - K, 0.0f)) : 0.0;
-                    const double s1 = warp_sum(v);
-                    const double s2 = warp_sum(v * v);
-                    if (lane == 0) {
-                        sm.red[((size_t)warp * ns + q) * 2 + 0] = s1;
-                        sm.red[((size_t)warp * ns + q) * 2 + 1] = s2;
-                    }
+                    // the double-float sums inlined: as a call they raise this kernel's
+                    // registers from 127 to 166
+                    const float v = (owner && active) ? caplet_payoff(a, Pf, Lm, K) : 0.0f;
+                    const float4 r = caplet_warp_sums_inline(DFloat{v, 0.0f}, df_square(v));
+                    if (lane == 0) reinterpret_cast<float4 *>(sm.red)[(size_t)warp * ns + q] = r;
                 }
                 __syncthreads();
                 if (tid < ns) {
-                    double s1 = 0.0, s2 = 0.0;
-                    for (int wv = 0; wv < (T >> 5); ++wv) {
-                        s1 += sm.red[((size_t)wv * ns + tid) * 2 + 0];
-                        s2 += sm.red[((size_t)wv * ns + tid) * 2 + 1];
-                    }
+                    double s1, s2;
+                    block_payoff_sums(a, sm.red, T >> 5, ns, tid, s1, s2);
                     double *acc = sm.bsum + 4 * ((size_t)(m - 1) * ns + tid);
                     kahan_add(acc + 0, acc + 1, s1);
                     kahan_add(acc + 2, acc + 3, s2);
