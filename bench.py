@@ -749,7 +749,8 @@ def run_mappings(args, rates=None):
     at 2^12 paths, for one lane per path (128 and 256 threads per block) and
     for 4, 8, 16 and 32 lanes per path; each with its fraction of the FP32
     roofline (3Q lane-ops per unit against the measured packed-FMA rate).
-    Returns the JSON line."""
+    --paths and --schemes narrow it to one size and a scheme (for a launch
+    list).  Returns the JSON line."""
     import torch
 
     from paper_1006_3340_gb300 import autotune, lll
@@ -761,12 +762,14 @@ def run_mappings(args, rates=None):
              [(f"tenor, {g} lanes/path", (0, 0, 0, 0, 0, g)) for g in (4, 8, 16, 32)] + \
              [("step-parallel (Picard)", (0, 0, 0, 0, 0, -1))]
     rows = []
-    for paths in (1 << 20, 1 << 12):
+    sizes = (args.paths,) if args.paths else (1 << 20, 1 << 12)
+    schemes = [s for s in args.schemes.split(",") if s in ("picard", "full")] or ["picard", "full"]
+    for paths in sizes:
         wl = workloads.large_single(paths=paths)
         x, W = lll.lll_build_nig_quadrature(wl.alpha, wl.beta, wl.dbar, wl.a, wl.Q)
         sim = lll.LevyLibor(wl, x, W)
         try:
-            for scheme in ("picard", "full"):
+            for scheme in schemes:
                 for name, cand in shapes:
                     if scheme == "full" and len(cand) > 5 and cand[5] < 0:
                         continue  # the full scheme's steps are sequential
