@@ -289,14 +289,14 @@ def run_batch(args, steps, warmup, with_cpu=True, with_e2e=True, rates=None):
     caplets = sum(wl.n * wl.strikes.shape[1] for wl in wls)
     b, keep = lll.lll_batch_init(inst)  # default stream, the one torch's events record on
     own = args.workload == "batch256"  # not the batch256 block of the default run
-    if own and args.launch:  # threads,blocks_per_sm,chunk_rows
-        shape = [int(v) for v in args.launch.split(",")][:3]
+    if own and args.launch:  # threads,blocks_per_sm,chunk_rows[,paths_per_thread], both schemes
+        shape = [int(v) for v in args.launch.split(",")][:4]
         lll.lll_batch_set_launch(b, *shape)
-        tuned = {"launch": shape, "ms": None, "tried": []}
+        tuned = {s: {"launch": shape, "ms": None, "tried": []} for s in schemes}
     elif own and args.no_tune:
-        tuned = {"launch": [0, 0, 0], "ms": None, "tried": []}
-    else:
-        tuned = autotune.tune_batch(b, inst, "full")  # one launch shape for both schemes
+        tuned = {s: {"launch": [0, 0, 0, 0], "ms": None, "tried": []} for s in schemes}
+    else:  # each scheme its own launch shape
+        tuned = {s: autotune.tune_batch(b, inst, s, repeats=1) for s in schemes}
     lll.lll_batch_use_graph(b, True)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -357,7 +357,8 @@ def run_batch(args, steps, warmup, with_cpu=True, with_e2e=True, rates=None):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             b2, keep2 = lll.lll_batch_init(inst)
-            lll.lll_batch_set_launch(b2, *tuned["launch"])
+            for s in schemes:
+                lll.lll_batch_set_launch(b2, *tuned[s]["launch"], scheme=s)
             for s in schemes:
                 lll.lll_batch_simulate(b2, lll.SCHEMES[s], 42)
                 for q, wl in enumerate(wls):
@@ -528,9 +529,10 @@ def run_single(args, wl, schemes, steps, warmup, dev, rank, world, local, with_c
                 autotune.apply(sims[s], shape)
                 tuned[s] = {"launch(threads,bps,chunk,ppt,lanes[,tenor])": shape, "ms": None}
     elif tune:
-        # one lane per path (paths per thread 1 or 2), and the tenor-parallel mapping
-        cands = tune_candidates or [(128, 0, 0, 1, 1), (256, 0, 0, 1, 1), (128, 0, 0, 1, 2), (256, 0, 0, 1, 2),
-                                    (0, 0, 0, 0, 0, 8), (0, 0, 0, 0, 0, 16), (0, 0, 0, 0, 0, -1)]
+        # one lane per path (one or two paths per thread), lane pairs sharing a
+        # path pair's nodes, and the tenor- and step-parallel mappings
+        cands = tune_candidates or [(128, 0, 0, 1, 1), (256, 0, 0, 1, 1), (128, 0, 0, 2, 1), (128, 0, 0, 1, 2),
+                                    (256, 0, 0, 1, 2), (0, 0, 0, 0, 0, 8), (0, 0, 0, 0, 0, 16), (0, 0, 0, 0, 0, -1)]
         for s in schemes:
             if s in ("picard", "full", "frozen"):
                 r = autotune.tune(sims[s], s, candidates=cands, repeats=tune_repeats, use_cache=False)

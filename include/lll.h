@@ -266,9 +266,17 @@ typedef struct lll_batch lll_batch;
  * an instance's LLL_EDOMAIN warning is accepted).  Inputs are copied. */
 int lll_batch_init(lll_batch **out, int n_inst, const lll_instance *inst, void *cuda_stream);
 
-/* lll_batch_set_launch -- threads per block, blocks per SM (0: occupancy
- * maximum), table rows per staged chunk (0: default). */
-int lll_batch_set_launch(lll_batch *b, int threads_per_block, int blocks_per_sm, int chunk_rows);
+/* lll_batch_set_launch -- the launch shape of scheme LLL_FULL or LLL_PICARD
+ * (-1: both): threads per block (0: 128), blocks per SM (0: occupancy
+ * maximum), table rows per staged chunk (0: default) and paths per thread
+ * (0 or 1: one; 2: two paths share every staged table load, for padded
+ * Q <= 64).  Each scheme keeps its own shape, schedule and graph: alternating
+ * schemes rebuilds nothing; a new shape rebuilds that scheme's on its next
+ * simulation.  Synchronises the stream.  LLL_EINVAL for values out of range;
+ * an unsupported combination is reported by the next lll_batch_simulate
+ * (LLL_EUNSUPPORTED). */
+int lll_batch_set_launch(lll_batch *b, int scheme, int threads_per_block, int blocks_per_sm, int chunk_rows,
+                         int paths_per_thread);
 
 /* lll_batch_use_graph -- enable: the first simulation of a scheme captures
  * its launch sequence (descriptor upload from pinned memory, reset of the

@@ -23,8 +23,9 @@ CACHE = os.path.join(_build.BUILD, "autotune.json")
 
 DEFAULT_CANDIDATES = [
     # (threads, blocks_per_sm, chunk_rows, paths_per_thread, lanes_per_path[, tenor lanes])
-    (t, 0, c, 1, l) for t, c, l in itertools.product((64, 128, 256), (0, 16), (1, 4))
-] + [(0, 0, 0, 0, 0, g) for g in (4, 8, 16, 32, -1)]
+    (t, 0, c, 1, l) for t, c, l in itertools.product((64, 128, 256), (0, 16), (1, 2, 4))
+] + [(t, 0, c, 2, 1) for t, c in itertools.product((64, 128), (0, 16))] \
+  + [(0, 0, 0, 0, 0, g) for g in (4, 8, 16, 32, -1)]
 
 
 def apply(sim: "lll.LevyLibor", cand) -> None:
@@ -105,16 +106,22 @@ def _timed(sim, scheme, paths) -> float:
     return sim.kernel_ms()[0]
 
 
-def tune_batch(b, instances, scheme: str,
-               candidates: Iterable[Tuple[int, int, int]] = ((64, 0, 0), (128, 0, 0), (256, 0, 0),
-                                                             (128, 0, 16), (128, 2, 0)),
+BATCH_CANDIDATES = [
+    # (threads, blocks_per_sm, chunk_rows, paths_per_thread); 64-thread blocks and
+    # two blocks per SM measured slowest on the 256-instance batch, and are left out
+    (128, 0, 0, 1), (256, 0, 0, 1), (128, 0, 16, 1), (128, 0, 0, 2), (128, 0, 16, 2),
+]
+
+
+def tune_batch(b, instances, scheme: str, candidates: Iterable[Tuple[int, int, int, int]] = BATCH_CANDIDATES,
                repeats: int = 2, seed: int = 42) -> dict:
-    """Same for a batch (threads, blocks_per_sm, chunk_rows); applies the best."""
+    """Same for a batch and one scheme (threads, blocks_per_sm, chunk_rows,
+    paths_per_thread); applies the best to that scheme only."""
     code = lll.SCHEMES[scheme]
     results = []
     for cand in candidates:
         try:
-            lll.lll_batch_set_launch(b, *cand)
+            lll.lll_batch_set_launch(b, *cand, scheme=code)
             lll.lll_batch_simulate(b, code, seed)
             t = []
             for _ in range(repeats):
@@ -126,5 +133,5 @@ def tune_batch(b, instances, scheme: str,
     if not results:
         raise RuntimeError("no batch launch shape ran")
     results.sort()
-    lll.lll_batch_set_launch(b, *results[0][1])
+    lll.lll_batch_set_launch(b, *results[0][1], scheme=code)
     return {"launch": list(results[0][1]), "ms": results[0][0], "tried": [[m, list(c)] for m, c in results]}

@@ -94,9 +94,9 @@ int launch_step_chunk(int QP, const PathArgs &a, uint64_t chunk_first, int Pc, f
                       float *Zm, int block0, double *partials, cudaStream_t st);
 struct LaunchPlan;
 int launch_plan(const LaunchPlan &plan, const PathArgs &a);
-bool batch_kernel_supported(int scheme, int QP);
-int batch_kernel_prepare(int scheme, int QP, size_t smem, int threads, int *blocks_per_sm);
-int launch_batch_kernel(int scheme, int QP, int grid, int threads, size_t smem, cudaStream_t st,
+bool batch_kernel_supported(int scheme, int QP, int R);
+int batch_kernel_prepare(int scheme, int QP, int R, size_t smem, int threads, int *blocks_per_sm);
+int launch_batch_kernel(int scheme, int QP, int R, int grid, int threads, size_t smem, cudaStream_t st,
                         const BatchArgs &b);
 
 // Launchers implemented in lll_tables.cu.

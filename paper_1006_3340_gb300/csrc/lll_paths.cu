@@ -388,15 +388,16 @@ __global__ void __launch_bounds__(Bounds<LB>::threads, Bounds<LB>::blocks) path_
 // the end (longest-processing-time-first list scheduling, Graham 1969).  Each
 // item writes its payoff sums to its own segment, and a second kernel adds the
 // segments of each instance in tile order, so the results do not depend on
-// which block ran which item.
-template <int SCHEME, int QP>
+// which block ran which item.  R paths per thread, as in path_kernel (a tile
+// is T R paths).
+template <int SCHEME, int QP, int R>
 __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchArgs b)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int NST = (SCHEME == PICARD) ? 2 : 1;
     const int T = blockDim.x, tid = threadIdx.x;
     const Smem sm = carve(smem_raw, QP, b.n_max, b.ns_max, T, b.chunk_rows);
-    float *st = b.state + (size_t)blockIdx.x * NST * b.n_max * T + tid;
+    float *st = b.state + (size_t)blockIdx.x * R * NST * b.n_max * T + tid;
     int cur = -1;
     __shared__ PathArgs sa; // the current instance's arguments
     __shared__ int claimed;
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(kMaxThreads) batch_kernel(const BatchArgs b)
         }
         for (int e = tid; e < 4 * a->n * a->ns; e += T) sm.bsum[e] = 0.0;
         const uint2 tr = b.item_tiles[it];
-        for (uint32_t t = tr.x; t < tr.y; ++t) run_tile<SCHEME, QP, 1>(*a, sm, st, t);
+        for (uint32_t t = tr.x; t < tr.y; ++t) run_tile<SCHEME, QP, R>(*a, sm, st, t);
         __syncthreads();
         double *out = b.partials + b.seg_off[it];
         for (int e = tid; e < a->n * a->ns; e += T) {
@@ -476,48 +477,52 @@ KernelFn pick(int scheme, int QP, int R, int T)
 
 typedef void (*BatchFn)(const BatchArgs);
 
-BatchFn pick_batch(int scheme, int QP)
+template <int SCHEME>
+BatchFn pick_batch_s(int QP, int R)
 {
-    if (scheme == PICARD) {
+    if (R == 2) { // two paths per thread: compiled where the registers of two node arrays fit
         switch (QP) {
-        case 16: return batch_kernel<PICARD, 16>;
-        case 32: return batch_kernel<PICARD, 32>;
-        case 64: return batch_kernel<PICARD, 64>;
-        case 96: return batch_kernel<PICARD, 96>;
-        case 128: return batch_kernel<PICARD, 128>;
+        case 16: return batch_kernel<SCHEME, 16, 2>;
+        case 32: return batch_kernel<SCHEME, 32, 2>;
+        case 64: return batch_kernel<SCHEME, 64, 2>;
         default: return nullptr;
         }
     }
-    if (scheme == FULL) {
-        switch (QP) {
-        case 16: return batch_kernel<FULL, 16>;
-        case 32: return batch_kernel<FULL, 32>;
-        case 64: return batch_kernel<FULL, 64>;
-        case 96: return batch_kernel<FULL, 96>;
-        case 128: return batch_kernel<FULL, 128>;
-        default: return nullptr;
-        }
+    if (R != 1) return nullptr;
+    switch (QP) {
+    case 16: return batch_kernel<SCHEME, 16, 1>;
+    case 32: return batch_kernel<SCHEME, 32, 1>;
+    case 64: return batch_kernel<SCHEME, 64, 1>;
+    case 96: return batch_kernel<SCHEME, 96, 1>;
+    case 128: return batch_kernel<SCHEME, 128, 1>;
+    default: return nullptr;
     }
+}
+
+BatchFn pick_batch(int scheme, int QP, int R)
+{
+    if (scheme == PICARD) return pick_batch_s<PICARD>(QP, R);
+    if (scheme == FULL) return pick_batch_s<FULL>(QP, R);
     return nullptr;
 }
 
 }  // namespace
 
-bool batch_kernel_supported(int scheme, int QP) { return pick_batch(scheme, QP) != nullptr; }
+bool batch_kernel_supported(int scheme, int QP, int R) { return pick_batch(scheme, QP, R) != nullptr; }
 
-int batch_kernel_prepare(int scheme, int QP, size_t smem, int threads, int *blocks_per_sm)
+int batch_kernel_prepare(int scheme, int QP, int R, size_t smem, int threads, int *blocks_per_sm)
 {
-    BatchFn f = pick_batch(scheme, QP);
+    BatchFn f = pick_batch(scheme, QP, R);
     if (!f) return (int)cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, f, threads, smem);
 }
 
-int launch_batch_kernel(int scheme, int QP, int grid, int threads, size_t smem, cudaStream_t st,
+int launch_batch_kernel(int scheme, int QP, int R, int grid, int threads, size_t smem, cudaStream_t st,
                         const BatchArgs &b)
 {
-    BatchFn f = pick_batch(scheme, QP);
+    BatchFn f = pick_batch(scheme, QP, R);
     if (!f) return (int)cudaErrorInvalidValue;
     f<<<grid, threads, smem, st>>>(b);
     return (int)cudaGetLastError();

@@ -99,7 +99,7 @@ def load():
         "lll_gemm_bf16": (I, [I, I, I, V, I, V, I, I, I, I, I, V, V, V, V]),
         "lll_measure_pipe_rates": (I, [_dp, I]),
         "lll_batch_init": (I, [ctypes.POINTER(V), I, ctypes.POINTER(lll_instance), V]),
-        "lll_batch_set_launch": (I, [V, I, I, I]),
+        "lll_batch_set_launch": (I, [V, I, I, I, I, I]),
         "lll_batch_use_graph": (I, [V, I]),
         "lll_batch_simulate": (I, [V, I, U64]),
         "lll_batch_prices": (I, [V, I, _dp, _dp]),
@@ -331,8 +331,11 @@ def lll_batch_init(instances, stream: int = 0):
     return h, keep
 
 
-def lll_batch_set_launch(b, threads=0, blocks_per_sm=0, chunk_rows=0):
-    _check(load().lll_batch_set_launch(b, int(threads), int(blocks_per_sm), int(chunk_rows)))
+def lll_batch_set_launch(b, threads=0, blocks_per_sm=0, chunk_rows=0, paths_per_thread=0, scheme=-1):
+    """Launch shape of ``scheme`` (LLL_FULL, LLL_PICARD, a name, or -1: both)."""
+    sc = SCHEMES[scheme] if isinstance(scheme, str) else int(scheme)
+    _check(load().lll_batch_set_launch(b, sc, int(threads), int(blocks_per_sm), int(chunk_rows),
+                                       int(paths_per_thread)))
 
 
 def lll_batch_use_graph(b, enable=True):

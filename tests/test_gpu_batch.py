@@ -89,9 +89,11 @@ def test_claimed_items_run_every_tile_once(lll):
     order that changes from launch to launch.  Repeated launches give
     bit-identical prices; instance 0 (Philox word 1 = 0, as a single context
     draws) equals its own single-context simulation of the same paths, and
-    every instance equals a launch with 64-thread tiles (other tiles, other
-    items), both within FP64 rounding of the grouping -- a tile run twice or
-    not at all would move a price by about 1/(tiles of the instance)."""
+    every instance equals a launch with 64-thread tiles and one with two paths
+    per thread (other tiles, other items), all within FP64 rounding of the
+    grouping -- a tile run twice or not at all would move a price by about
+    1/(tiles of the instance).  The Picard scheme runs between the full
+    scheme's launches, each scheme on its own cached schedule."""
     inst = _instances(8, 1 << 21, seed=13)
     b, keep = lll.lll_batch_init(inst)
     try:
@@ -99,16 +101,22 @@ def test_claimed_items_run_every_tile_once(lll):
         for _ in range(3):
             lll.lll_batch_simulate(b, lll.LLL_FULL, 5)
             runs.append(_prices(lll, b, inst))
+            lll.lll_batch_simulate(b, lll.LLL_PICARD, 5)  # the other scheme's schedule in between
         lll.lll_batch_set_launch(b, 64, 0, 0)
         lll.lll_batch_simulate(b, lll.LLL_FULL, 5)
         small = _prices(lll, b, inst)
+        # two paths per thread (tiles of 256 paths): the same per-path arithmetic
+        lll.lll_batch_set_launch(b, 128, 0, 16, 2, scheme="full")
+        lll.lll_batch_simulate(b, lll.LLL_FULL, 5)
+        pairs = _prices(lll, b, inst)
     finally:
         lll.lll_batch_destroy(b)
     for r in runs[1:]:
         for (p0, _), (p1, _) in zip(runs[0], r):
             assert np.array_equal(p0, p1)
-    for q, ((p0, _), (ps, _)) in enumerate(zip(runs[0], small)):
+    for q, ((p0, _), (ps, _), (pp, _)) in enumerate(zip(runs[0], small, pairs)):
         assert np.allclose(p0, ps, rtol=1e-12, atol=1e-18), q
+        assert np.allclose(p0, pp, rtol=1e-12, atol=1e-18), q
     wl, x, W = inst[0]
     sim = lll.LevyLibor(wl, x, W)
     try:
