@@ -106,7 +106,7 @@ __global__ void finalize_kernel(const double *partials, int grid, int n_out, dou
     sums[e] = s;
 }
 
-// Per instance of a batch: add its segment partials in block order.
+// Per instance of a batch: add the partials of its work items in tile order.
 __global__ void batch_finalize_kernel(const double *partials, const size_t *seg_off, const int *inst_seg_ptr,
                                       const int *inst_segs, const size_t *out_off, const int *out_count,
                                       double *sums)
