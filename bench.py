@@ -617,8 +617,10 @@ def run_single(args, wl, schemes, steps, warmup, dev, rank, world, local, with_c
         ach = units * 3 * wl.Q / (ms * 1e-3) / 1e12
         shape = tuned.get(s, {}).get("launch(threads,bps,chunk,ppt,lanes[,tenor])")
         lanes = shape[4] if shape and shape[4] else 1
+        ppt = shape[3] if shape and shape[3] else 1
         tenor = shape[5] if shape and len(shape) > 5 else 0
-        traffic = (_traffic(f"{s}/QP{wl.Q}/lanes{lanes}") if wl.paths == 1 << 20 and not tenor else None)
+        key = f"{s}/QP{wl.Q}/lanes{lanes}" + (f"/ppt{ppt}" if ppt > 1 else "")
+        traffic = (_traffic(key) if wl.paths == 1 << 20 and not tenor else None)
         r = {"bound": "alu", "achieved": ach, "peak": pk["fp32"], "unit": "TFP32-lane-op/s",
              "frac": ach / pk["fp32"], "frac_of_nominal_128_lanes": ach / pk["fp32_nominal"], "traffic": traffic,
              "kernel": (f"{s} tenor-parallel kernel ({tenor} lanes per path), QP={wl.Q}" if tenor
