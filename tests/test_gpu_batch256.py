@@ -11,7 +11,9 @@ checked against the FP64 oracle run with instance q:
     under the full scheme, within 1e-7;
   * four paths sampled across every instance's budget (so they fall in
     different tiles and work items of the schedule), and 32 of the
-    N = 80 instance, within 1e-5 relative on every recorded rate.
+    N = 80 instance, within 1e-5 relative on every recorded rate;
+  * both under the library's default launch shape and under the one the
+    bench's tuner picks for this batch (two paths per thread).
 """
 import numpy as np
 import pytest
@@ -22,6 +24,7 @@ from paper_1006_3340_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
 CODES = {"picard": ora.PICARD, "full": ora.FULL}
+SHAPES = (None, (128, 0, 16, 2))
 
 
 @pytest.fixture(scope="module")
@@ -50,11 +53,16 @@ def batch256(lll):
         for q in range(len(wls)):
             lll.lll_batch_set_snapshots(b, q, counts[q], strides[q])
         lll.lll_batch_use_graph(b, True)
-        for scheme in ("picard", "full"):
-            lll.lll_batch_simulate(b, lll.SCHEMES[scheme], 42)
-            prices = [lll.lll_batch_prices(b, q, wl.n, wl.strikes.shape[1])[0] for q, wl in enumerate(wls)]
-            snaps = [lll.lll_batch_get_paths(b, q, wl.n, 0, counts[q]) for q, wl in enumerate(wls)]
-            out[scheme] = (prices, snaps)
+        # the library's default shape, then the one the bench's tuner picks on
+        # this batch (128 threads, 16-row chunks, two paths per thread)
+        for shape in SHAPES:
+            if shape is not None:
+                lll.lll_batch_set_launch(b, *shape)
+            for scheme in ("picard", "full"):
+                lll.lll_batch_simulate(b, lll.SCHEMES[scheme], 42)
+                prices = [lll.lll_batch_prices(b, q, wl.n, wl.strikes.shape[1])[0] for q, wl in enumerate(wls)]
+                snaps = [lll.lll_batch_get_paths(b, q, wl.n, 0, counts[q]) for q, wl in enumerate(wls)]
+                out[scheme, shape] = (prices, snaps)
     finally:
         lll.lll_batch_destroy(b)
     return inst, counts, strides, q_long, out
@@ -63,14 +71,15 @@ def batch256(lll):
 @pytest.mark.parametrize("scheme", ["picard", "full"])
 def test_smallest_budget_instances_match_oracle_prices(batch256, scheme):
     inst, _, _, _, out = batch256
-    prices, _ = out[scheme]
     smallest = min(wl.paths for wl, _, _ in inst)
     checked = 0
     for q, (wl, x, W) in enumerate(inst):
         if wl.paths != smallest or (scheme == "full" and wl.N > 40):
             continue
         ref = ora.simulate(ora.OracleModel(wl, x, W), CODES[scheme], npaths=wl.paths, seed=42, inst=q)
-        assert np.abs(prices[q] - ref["price"]).max() <= 1e-7, (q, wl.N)
+        for shape in SHAPES:
+            prices, _ = out[scheme, shape]
+            assert np.abs(prices[q] - ref["price"]).max() <= 1e-7, (q, wl.N, shape)
         checked += 1
     assert checked == (35 if scheme == "picard" else 17)
 
@@ -78,15 +87,16 @@ def test_smallest_budget_instances_match_oracle_prices(batch256, scheme):
 @pytest.mark.parametrize("scheme", ["picard", "full"])
 def test_sampled_paths_of_every_instance_match_oracle(batch256, scheme):
     inst, counts, strides, q_long, out = batch256
-    _, snaps = out[scheme]
     worst = 0.0
     for q, (wl, x, W) in enumerate(inst):
         idx = np.arange(counts[q], dtype=np.uint64) * np.uint64(strides[q])
         ref = ora.simulate_paths(ora.OracleModel(wl, x, W), CODES[scheme], idx, seed=42, inst=q)
         mask = ~np.isnan(ref["snap"])
-        got = snaps[q].astype(np.float64)
-        assert np.array_equal(mask, ~np.isnan(got)), q
-        rel = np.abs(np.expm1(got[mask] - ref["snap"][mask])).max()
-        assert rel <= 1e-5, (q, wl.N, rel)
-        worst = max(worst, rel)
+        for shape in SHAPES:
+            _, snaps = out[scheme, shape]
+            got = snaps[q].astype(np.float64)
+            assert np.array_equal(mask, ~np.isnan(got)), (q, shape)
+            rel = np.abs(np.expm1(got[mask] - ref["snap"][mask])).max()
+            assert rel <= 1e-5, (q, wl.N, rel, shape)
+            worst = max(worst, rel)
     assert inst[q_long][0].N == 80 and counts[q_long] == 32
