@@ -531,8 +531,9 @@ def run_single(args, wl, schemes, steps, warmup, dev, rank, world, local, with_c
     elif tune:
         # one lane per path (one or two paths per thread), lane pairs sharing a
         # path pair's nodes, and the tenor- and step-parallel mappings
-        cands = tune_candidates or [(128, 0, 0, 1, 1), (256, 0, 0, 1, 1), (128, 0, 0, 2, 1), (128, 0, 0, 1, 2),
-                                    (256, 0, 0, 1, 2), (0, 0, 0, 0, 0, 8), (0, 0, 0, 0, 0, 16), (0, 0, 0, 0, 0, -1)]
+        cands = tune_candidates or [(128, 0, 0, 1, 1), (256, 0, 0, 1, 1), (128, 0, 16, 1, 1), (128, 0, 0, 2, 1),
+                                    (128, 0, 16, 2, 1), (128, 0, 0, 1, 2), (256, 0, 0, 1, 2), (0, 0, 0, 0, 0, 8),
+                                    (0, 0, 0, 0, 0, 16), (0, 0, 0, 0, 0, -1)]
         for s in schemes:
             if s in ("picard", "full", "frozen"):
                 r = autotune.tune(sims[s], s, candidates=cands, repeats=tune_repeats, use_cache=False)
