@@ -105,3 +105,18 @@ def test_calls_on_null_context_fail_cleanly(lll):
     assert lib.lll_simulate(None, 1, 0, 10, 42) == -1
     assert lib.lll_set_strikes(None, 1, None) == -1
     lib.lll_destroy(None)
+
+
+def test_batch_calls_on_null_handle_fail_cleanly(lll):
+    """The batch entry points check their handle and arguments before any CUDA
+    call (so these run without a GPU)."""
+    lib = lll.load()
+    assert lib.lll_batch_init(None, 1, None, None) == -1
+    assert lib.lll_batch_set_launch(None, -1, 128, 0, 0, 2) == -1
+    assert lib.lll_batch_use_graph(None, 1) == -1
+    assert lib.lll_batch_simulate(None, lll.LLL_FULL, 42) == -1
+    assert lib.lll_batch_prices(None, 0, None, None) == -1
+    assert lib.lll_batch_set_snapshots(None, 0, 1, 1) == -1
+    assert lib.lll_batch_get_paths(None, 0, 0, 1, None) == -1
+    assert lib.lll_batch_kernel_ms(None, None) == -1
+    lib.lll_batch_destroy(None)
