@@ -126,3 +126,21 @@ def test_claimed_items_run_every_tile_once(lll):
     finally:
         sim.close()
     assert np.allclose(runs[0][0][0], p, rtol=1e-12, atol=1e-18)
+
+
+def test_launch_shape_validation(lll):
+    """Out-of-range launch values are refused with LLL_EINVAL and leave the
+    batch usable."""
+    inst = _instances(2, 2 * 300, seed=3)
+    b, keep = lll.lll_batch_init(inst)
+    try:
+        for args, kw in (((128, 0, 0, 3), {}), ((100, 0, 0, 1), {}), ((128, -1, 0, 1), {}),
+                         ((128, 0, 0, 1), {"scheme": 5})):
+            with pytest.raises(lll.LLLError) as e:
+                lll.lll_batch_set_launch(b, *args, **kw)
+            assert e.value.code == lll.LLL_EINVAL
+        lll.lll_batch_simulate(b, lll.LLL_PICARD, 42)
+        p, _ = lll.lll_batch_prices(b, 0, inst[0][0].n, inst[0][0].strikes.shape[1])
+        assert np.all(np.isfinite(p))
+    finally:
+        lll.lll_batch_destroy(b)
