@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) mlp_path_kernel(const PathArgs
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, T = kWarps * 32;
     const int gq = lane >> 2, tq = lane & 3;
-    const int n = a.n, s = a.s, S = a.S, ns = a.ns, N = n + 1;
+    const int n = a.n, s = a.s, S = a.S, ns = a.ns;
     constexpr int upitch = KT0 * 16 + 8;
     MlpSmem sm;
     {
