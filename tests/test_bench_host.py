@@ -67,3 +67,25 @@ def test_training_flop_count():
     assert f == steps * 8192 * 6.0 * 39432
     fv = b._train_flop(workloads.long_dated(), 256, 4, 1, 263296, 20, 4096)
     assert fv == ((1 << 16) * 8 // 4096) * 20 * 4096 * 6.0 * 263296
+
+
+def test_traffic_entries_follow_source_hashes(tmp_path):
+    """A DRAM-traffic entry counts only while every source it lists still has
+    the SHA-1 it was measured with; otherwise, and for unknown keys, the bench
+    reports null."""
+    import hashlib
+    import json
+
+    b = _bench()
+    csrc = tmp_path / "paper_1006_3340_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "k.cu").write_text("kernel v1")
+    (tmp_path / "profiles").mkdir()
+    entry = {"dram_bytes_read": 10.0, "dram_bytes_write": 2.0,
+             "sources": {"k.cu": hashlib.sha1(b"kernel v1").hexdigest()}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"x": entry}))
+    b.ROOT = str(tmp_path)
+    assert b._traffic("x") == 12.0
+    assert b._traffic("missing") is None
+    (csrc / "k.cu").write_text("kernel v2")
+    assert b._traffic("x") is None
