@@ -144,3 +144,30 @@ def test_launch_shape_validation(lll):
         assert np.all(np.isfinite(p))
     finally:
         lll.lll_batch_destroy(b)
+
+
+def test_batch_with_96_nodes(lll):
+    """Instances on a 96-node rule: one path per thread against the oracle;
+    two paths per thread (compiled for up to 64 padded nodes) is refused with
+    LLL_EUNSUPPORTED and leaves the batch usable."""
+    import dataclasses
+
+    inst = []
+    for wl in workloads.batched_instances(n_inst=3, total_paths=3 * 400, seed=21):
+        wl = dataclasses.replace(wl, Q=96, paths=max(wl.paths, 1))
+        x, W = quadrature.rule_for(wl)
+        inst.append((wl, x, W))
+    b, keep = lll.lll_batch_init(inst)
+    try:
+        lll.lll_batch_set_launch(b, 128, 0, 0, 2, scheme="picard")
+        with pytest.raises(lll.LLLError) as e:
+            lll.lll_batch_simulate(b, lll.LLL_PICARD, 42)
+        assert e.value.code == lll.LLL_EUNSUPPORTED
+        lll.lll_batch_set_launch(b, 128, 0, 0, 1, scheme="picard")
+        lll.lll_batch_simulate(b, lll.LLL_PICARD, 42)
+        got = _prices(lll, b, inst)
+    finally:
+        lll.lll_batch_destroy(b)
+    for q, (wl, x, W) in enumerate(inst):
+        ref = ora.simulate(ora.OracleModel(wl, x, W), ora.PICARD, seed=42, inst=q)
+        assert np.abs(got[q][0] - ref["price"]).max() <= 1e-7, (q, wl.N)
